@@ -1,0 +1,384 @@
+"""Benchmark: batched one-sided Jacobi SVD on GB300.
+
+Workload (one step): the 128x64 tall batch in both precisions -- 10,000 FP64
+matrices Q1 diag(sigma) Q2^T with geometric sigma from 1 to 1e-6 and 10,000
+FP32 matrices with sigma from 1 to 1e-3 (Haar Q1, Q2; synthetic, seeded),
+nb = 16, full U, Sigma, V.  Metric: matrices/s (whole job, all ranks).
+
+Reported on one JSON line:
+  value       device-resident throughput (inputs in HBM before timing)
+  e2e         the same through the public API with host buffers: pinned
+              H2D of A and D2H of Sigma, U, V, info inside the timed region
+  roofline    the dominant kernel (FP64 fused SVD) against the FP64 pipe
+  cpu_baseline the CPU oracle (OpenMP over matrices) on a bounded sample
+  plain_fp64  the paper's baseline path (inner solver to convergence, no
+              masks) on the FP64 batch, when built, for "vs plain FP64"
+With --impl reference the CPU oracle alone runs as the reference arm.
+Multi-GPU (torchrun): every rank solves its own 10,000 + 10,000 matrices
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+U64, U32 = 2.0 ** -53, 2.0 ** -24
+M, N, NB = 128, 64, 16
+BATCH = 10000
+TOL_K = 30
+# FP64 / FP32 pipe peaks of GB300 from unit counts and the maximum SM clock:
+# 152 SMs x 2 FP64 FMA/clk/SM (resp. 128 FP32 FMA/clk/SM) x 2 flop x 2.07 GHz.
+PEAK_FP64 = 152 * 2 * 2 * 2.07e9
+PEAK_FP32 = 152 * 128 * 2 * 2.07e9
+# DRAM bytes per matrix of the FP64 fused kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum over a 2,000-matrix launch),
+# valid while the kernel source is unchanged (sha1 prefix below).
+TRAFFIC_PER_MATRIX = {"892677d64a86": 140.6e3}
+KERNEL_SRC = os.path.join(ROOT, "paper_2601_17979_gb300", "csrc", "gesvj_fused.cuh")
+
+
+def measured_traffic(batch):
+    import hashlib
+    h = hashlib.sha1(open(KERNEL_SRC, "rb").read()).hexdigest()[:12]
+    per = TRAFFIC_PER_MATRIX.get(h)
+    return None if per is None else per * batch
+
+
+def pair_flops(m, n, nb, cplx=False):
+    """Algorithmic flops of one block pair: Gram 4 m nb^2, A update 8 m nb^2,
+    V update 8 n nb^2, one inner sweep 72 nb^3 (x4 for complex)."""
+    f = 12 * m * nb * nb + 8 * n * nb * nb + 72 * nb ** 3
+    return 4 * f if cplx else f
+
+
+def matrix_flops(m, n, nb, sweeps):
+    """Executed sweeps: all but the last do full pair steps; the last (the
+    sweep that found every block diagonal) forms the Gram blocks only."""
+    l = max(2, -(-n // nb))
+    pairs = l * (l - 1) // 2
+    sweeps = np.asarray(sweeps, dtype=np.float64)
+    return (np.maximum(sweeps - 1, 0) * pairs * pair_flops(m, n, nb)
+            + pairs * 4 * m * nb * nb + 3 * m * n).sum()
+
+
+def oracle_flops(m, n, sweeps):
+    """Alg. 2 work: (12 m + 6 n) flops per column pair per sweep."""
+    return float(np.sum(np.asarray(sweeps, dtype=np.float64) * (12 * m + 6 * n) * n * (n - 1) / 2))
+
+
+def residuals(A, S, U, V):
+    """||A - U S V^H||_F / ||A||_F and ||U^H U - I||_F, ||V^H V - I||_F in FP64."""
+    A, S, U, V = (np.asarray(x, dtype=np.float64) for x in (A, S, U, V))
+    k = S.shape[0]
+    return {"resid": float(np.linalg.norm(A - (U * S) @ V.T) / np.linalg.norm(A)),
+            "orth_u": float(np.linalg.norm(U.T @ U - np.eye(k))),
+            "orth_v": float(np.linalg.norm(V.T @ V - np.eye(k)))}
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id, self.proc, self.lines = gpu_id, None, []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx = max(mx, float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_uuid(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return "0"
+
+
+def build_inputs(rank: int, count: int):
+    A64 = synth.uniform_batch("tall128x64_f64", count, start=rank * count)
+    A32 = synth.uniform_batch("tall128x64_f32", count, start=rank * count)
+    return A64, A32
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle on the host cores, bounded samples."""
+    import oracle
+    if rank != 0:
+        return
+    per = args.ref_sample
+    A64 = synth.matrices("tall128x64_f64", range(per))
+    A32 = synth.matrices("tall128x64_f32", range(per))
+    O = oracle.default()
+    cores = len(os.sched_getaffinity(0))
+    times, threads = [], 0
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r1 = O.gesvj(A64, tol=TOL_K * U64)
+        r2 = O.gesvj(A32, tol=TOL_K * U64)
+        dt = time.perf_counter() - t0
+        threads = r1["threads"]
+        if s >= args.warmup:
+            times.append(dt)
+    t = float(np.mean(times))
+    value = 2 * per / t
+    line = {
+        "impl": "reference", "metric": "batch SVD matrices/s (tall 128x64, FP64+FP32)",
+        "value": value, "unit": "matrices/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(world, per * 2),
+        "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{per} FP64 + {per} FP32 matrices 128x64 per step, Alg. 2 (unblocked), "
+                                   f"OpenMP over matrices, {cores} cores available"},
+        "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(world, per_rank):
+    return {"workload": "tall128x64: 10,000 FP64 (sigma geometric 1..1e-6) + 10,000 FP32 "
+                        "(1..1e-3) matrices 128x64 = Q1 diag(sigma) Q2^T, Haar Q1, Q2",
+            "m": M, "n": N, "nb": NB, "matrices_per_rank": per_rank, "tol": f"{TOL_K} u",
+            "jobs": "U, Sigma, V", "l2": "inputs (983 MB per rank) larger than L2 (129 MB)",
+            "parallelism": f"replicas x{world} (independent matrices per rank)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=BATCH, help="matrices per precision per rank")
+    ap.add_argument("--cpu-sample", type=int, default=3000, help="oracle sample per precision")
+    ap.add_argument("--ref-sample", type=int, default=512, help="reference arm: matrices per precision per step")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import paper_2601_17979_gb300 as bsvd
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    bsvd.build()
+
+    A64h, A32h = build_inputs(rank, args.batch)
+    B = args.batch
+    # column-major device inputs and preallocated outputs
+    def to_dev(Ah, dt):
+        return torch.from_numpy(Ah).to(dev).transpose(1, 2).contiguous().transpose(1, 2)
+    A64 = to_dev(A64h, torch.float64)
+    A32 = to_dev(A32h, torch.float32)
+
+    def outputs(dt, rdt):
+        return (torch.empty((B, N), dtype=rdt, device=dev), bsvd.empty_column_major(B, M, N, dt, dev),
+                bsvd.empty_column_major(B, N, N, dt, dev), torch.empty(B, dtype=torch.int32, device=dev),
+                torch.empty(B, dtype=torch.int32, device=dev))
+    o64 = outputs(torch.float64, torch.float64)
+    o32 = outputs(torch.float32, torch.float32)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        bsvd.gesvj(A64, nb=NB, tol=TOL_K * U64, out=o64)
+        if ev is not None:
+            ev[1].record(stream)
+        bsvd.gesvj(A32, nb=NB, tol=TOL_K * U32, out=o32)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    sampler = ClockSampler(gpu_uuid(torch, dev))
+    barrier()
+    with sampler:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for s in range(args.steps):
+            step(evs[s])
+        t_end.record(stream)
+        barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    k64 = [e[0].elapsed_time(e[1]) for e in evs]
+    k32 = [e[1].elapsed_time(e[2]) for e in evs]
+    ms_step = total_ms / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = 2 * B * world / (ms_step * 1e-3)
+
+    # results of the last step: convergence and a bounds check on a sample
+    info64, sw64 = o64[3].cpu().numpy(), o64[4].cpu().numpy()
+    info32, sw32 = o32[3].cpu().numpy(), o32[4].cpu().numpy()
+    flops64 = matrix_flops(M, N, NB, sw64)
+    flops32 = matrix_flops(M, N, NB, sw32)
+    t64 = float(np.mean(k64)) * 1e-3
+    t32 = float(np.mean(k32)) * 1e-3
+    worst = {}
+    for Ah, o, u in ((A64h, o64, U64), (A32h, o32, U32)):
+        for i in range(0, B, max(1, B // 8)):
+            meas = residuals(Ah[i], o[0][i].cpu().numpy(), o[1][i].cpu().numpy(), o[2][i].cpu().numpy())
+            for key, val in meas.items():
+                worst[key] = max(worst.get(key, 0.0), val / (20 * N * u))
+
+    line = {
+        "metric": "batch SVD matrices/s (tall 128x64, FP64+FP32)", "value": value, "unit": "matrices/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+        "data": "synthetic", "config": config_dict(world, 2 * B),
+        "gpu_launches": 2 * args.steps,
+        "fp64": {"matrices_per_s": B / t64, "kernel_ms": t64 * 1e3, "gflops": flops64 / t64 / 1e9,
+                 "sweeps_mean": float(sw64.mean()), "sweeps_max": int(sw64.max()),
+                 "info_nonzero": int((info64 != 0).sum())},
+        "fp32": {"matrices_per_s": B / t32, "kernel_ms": t32 * 1e3, "gflops": flops32 / t32 / 1e9,
+                 "sweeps_mean": float(sw32.mean()), "sweeps_max": int(sw32.max()),
+                 "info_nonzero": int((info32 != 0).sum()),
+                 "roofline": {"bound": "alu", "achieved": flops32 / t32 / 1e12, "peak": PEAK_FP32 / 1e12,
+                              "unit": "TFLOP/s", "frac": flops32 / t32 / PEAK_FP32}},
+        "roofline": {"bound": "alu", "achieved": flops64 / t64 / 1e12, "peak": PEAK_FP64 / 1e12,
+                     "unit": "TFLOP/s", "frac": flops64 / t64 / PEAK_FP64, "traffic": measured_traffic(B),
+                     "kernel": "gesvj_fused_kernel<double,16,2,128>",
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"},
+        "accuracy_worst_over_bound": worst,
+        "clocks": sampler.summary(),
+    }
+
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        A64p = torch.from_numpy(A64h.transpose(0, 2, 1).copy()).pin_memory()
+        A32p = torch.from_numpy(A32h.transpose(0, 2, 1).copy()).pin_memory()
+        host_out = [tuple(torch.empty(t.shape, dtype=t.dtype).pin_memory() if t.dim() < 3 else
+                          torch.empty((t.shape[0], t.shape[2], t.shape[1]), dtype=t.dtype).pin_memory()
+                          for t in o) for o in (o64, o32)]
+        d64 = torch.empty((B, N, M), dtype=torch.float64, device=dev)
+        d32 = torch.empty((B, N, M), dtype=torch.float32, device=dev)
+        h2d = A64p.numel() * 8 + A32p.numel() * 4
+        d2h = sum(t.numel() * t.element_size() for o in (o64, o32) for t in o)
+
+        def e2e_step():
+            d64.copy_(A64p, non_blocking=True)
+            d32.copy_(A32p, non_blocking=True)
+            bsvd.gesvj(d64.transpose(1, 2), nb=NB, tol=TOL_K * U64, out=o64)
+            bsvd.gesvj(d32.transpose(1, 2), nb=NB, tol=TOL_K * U32, out=o32)
+            for o, ho in zip((o64, o32), host_out):
+                for t, h in zip(o, ho):
+                    h.copy_(t if t.dim() < 3 else t.transpose(1, 2), non_blocking=True)
+        e2e_step()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        b.record(stream)
+        barrier()
+        e_ms = a.elapsed_time(b) / args.steps
+        if dist is not None:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        line["e2e"] = {"value": 2 * B * world / (e_ms * 1e-3), "unit": "matrices/s",
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                       "ms_per_step": e_ms}
+        line["gpu_launches"] += 2 * args.steps
+
+    # CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        S = min(args.cpu_sample, B)
+        O = oracle.default()
+        t0 = time.perf_counter()
+        r1 = O.gesvj([A64h[i] for i in range(S)], tol=TOL_K * U64)
+        r2 = O.gesvj([A32h[i] for i in range(S)], tol=TOL_K * U64)
+        dt = time.perf_counter() - t0
+        fl = oracle_flops(M, N, r1["sweeps"]) + oracle_flops(M, N, r2["sweeps"])
+        line["cpu_baseline"] = {
+            "value": 2 * S / dt, "unit": "matrices/s", "cores": r1["threads"], "kind": "oracle",
+            "sample": f"first {S} FP64 + {S} FP32 matrices of the same workload, Alg. 2 in FP64, "
+                      f"OpenMP over matrices ({dt:.1f} s)", "gflops": fl / dt / 1e9}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

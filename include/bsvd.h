@@ -1,0 +1,149 @@
+/*
+ * bsvd.h -- batched one-sided Jacobi SVD on NVIDIA GB300 (sm_103a).
+ *
+ * Computes, for every matrix A_i (m_i x n_i) of a batch, the reduced SVD
+ *     A_i = U_i Sigma_i V_i^H,
+ * U_i: m_i x k_i and V_i: n_i x k_i with orthonormal columns, Sigma_i: k_i
+ * non-negative reals in descending order, k_i = min(m_i, n_i) (Sec. 1,
+ * Eq. svd, of Abdelfattah and Fasi, "An Efficient Batch Solver for the
+ * Singular Value Decomposition on GPUs").  The method is the blocked
+ * one-sided (Hestenes) Jacobi algorithm of Sec. 3 (Eq. block-gram, right-sv)
+ * run as in Sec. 4 (steps S1-S5) with the optimisations of Sec. 5-7: one
+ * inner Jacobi sweep per Gram block (Design-2), fused vector update
+ * (Design-3, Alg. 4) and per-matrix masking (Design-4).
+ *
+ * Conventions (all entry points):
+ *  - Storage is column-major with a leading dimension, LAPACK style.  Types:
+ *    s = float, d = double, c = complex float, z = complex double, complex
+ *    data interleaved (re, im).  Sigma is always real (float for s/c, double
+ *    for d/z).
+ *  - Every device pointer must be to memory of the current CUDA device; the
+ *    call is asynchronous on `stream` (a cudaStream_t, NULL = legacy default
+ *    stream) and returns after argument checks and kernel enqueue.
+ *  - A is read only.  The caller owns every buffer, including the workspace;
+ *    the library allocates no device memory.
+ *  - Status codes are synchronous (argument and launch errors).  On
+ *    BSVD_ERR_INVALID, bsvd_last_arg() gives the 1-based position of the
+ *    offending argument.  Per-matrix results go to d_info on the device:
+ *        0   converged (a full sweep in which no pair rotated);
+ *        k>0 not converged after k = max_sweeps sweeps (outputs still written);
+ *        -1  A_i holds a NaN or infinity (outputs set to NaN).
+ *  - m < n is solved on A^H (Sec. 6.2: A^H = V Sigma U^H).
+ *  - The sign (real) or phase (complex) of each singular-vector pair is
+ *    unspecified; within exactly repeated singular values any orthonormal
+ *    basis may be returned.
+ */
+#ifndef BSVD_H
+#define BSVD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BSVD_VERSION 1
+
+typedef struct bsvd_handle_s* bsvd_handle;
+
+typedef enum {
+    BSVD_OK = 0,
+    BSVD_ERR_INVALID = -1,          /* bad argument; see bsvd_last_arg()        */
+    BSVD_ERR_WORKSPACE = -2,        /* work_bytes smaller than the query result */
+    BSVD_ERR_CUDA = -3,             /* a CUDA call failed; see bsvd_last_cuda() */
+    BSVD_ERR_TIMEOUT = -4,          /* a bounded device wait expired            */
+    BSVD_ERR_NOT_IMPLEMENTED = -5,  /* shape/type/option combination not built  */
+    BSVD_ERR_NOMEM = -6             /* host allocation failed                   */
+} bsvd_status;
+
+typedef enum { BSVD_JOB_NONE = 0, BSVD_JOB_SOME = 1 } bsvd_job;   /* economy-size vectors */
+
+typedef enum {
+    BSVD_PATH_AUTO = 0,     /* fastest path that fits                                   */
+    BSVD_PATH_FUSED = 1,    /* one kernel per matrix, A and V resident on chip          */
+    BSVD_PATH_PLAIN = 2     /* the paper's baseline (Sec. 4): one launch per stage and
+                               round, inner eigensolver run to convergence, two-stage
+                               vector update, no masks; FP64 comparison path           */
+} bsvd_path;
+
+/* Solver options.  Zero-initialise, then set what you need; 0 = default. */
+typedef struct {
+    int nb;            /* block width (Sec. 4); 0 = chosen from n and the type            */
+    int max_sweeps;    /* outer sweep limit; 0 = 40                                        */
+    double tol;        /* pair rotates iff |g_ij| >= tol sqrt(g_ii g_jj) (Alg. 1, Alg. 2);
+                          0 = 30 u, u the unit roundoff of the type (Sec. 5.4, k = 30)      */
+    int inner_sweeps;  /* inner eigensolver sweeps per Gram block; 0 = 1 (Design-2, Sec. 5) */
+    int path;          /* bsvd_path                                                         */
+    int flags;         /* bit 0: skip the final orthogonality correction of V              */
+    int reserved[6];
+} bsvd_opts;
+
+/* Handle: caches device properties and per-device kernel set-up; owns no
+ * device memory.  Not thread-safe: use one handle per host thread. */
+bsvd_status bsvd_create(bsvd_handle* handle);
+bsvd_status bsvd_destroy(bsvd_handle handle);
+const char* bsvd_status_string(bsvd_status status);
+int bsvd_last_arg(bsvd_handle handle);          /* 1-based argument index of the last INVALID */
+int bsvd_last_cuda(bsvd_handle handle);         /* cudaError_t of the last ERR_CUDA            */
+int bsvd_version(void);
+
+/*
+ * Workspace query for one call.  dtype is 's', 'd', 'c' or 'z'.  For the
+ * strided form pass m_arr = &m, n_arr = &n and uniform = 1; for the
+ * pointer-array form pass the host arrays m[batch], n[batch] and uniform = 0.
+ * *bytes receives the size of d_work the call needs (possibly 0).
+ */
+bsvd_status bsvd_gesvj_workspace(bsvd_handle handle, char dtype, int batch, const int* m_arr,
+                                 const int* n_arr, int uniform, bsvd_job jobu, bsvd_job jobv,
+                                 const bsvd_opts* opts, size_t* bytes);
+
+/*
+ * Strided batch: every matrix has the same m and n; matrix i of X starts at
+ * dX + i * strideX (in elements).  Arguments (1-based positions for
+ * bsvd_last_arg):
+ *   1 handle   2 jobu   3 jobv   4 batch >= 0   5 m >= 0   6 n >= 0
+ *   7 dA (device, read only)   8 lda >= max(1, m)   9 strideA >= lda * n
+ *  10 dS (device, k reals per matrix)   11 strideS >= k
+ *  12 dU (device; ignored when jobu = NONE)   13 ldu >= max(1, m)   14 strideU >= ldu * k
+ *  15 dV (device; ignored when jobv = NONE)   16 ldv >= max(1, n)   17 strideV >= ldv * k
+ *  18 d_info (device, batch ints)   19 d_sweeps (device, batch ints, or NULL)
+ *  20 d_work (device, 16-byte aligned)   21 work_bytes   22 opts (NULL = defaults)
+ *  23 stream
+ */
+#define BSVD_STRIDED_ARGS(T, R)                                                             \
+    bsvd_handle handle, bsvd_job jobu, bsvd_job jobv, int batch, int m, int n,               \
+    const T* dA, int lda, long long strideA, R* dS, long long strideS,                       \
+    T* dU, int ldu, long long strideU, T* dV, int ldv, long long strideV,                    \
+    int* d_info, int* d_sweeps, void* d_work, size_t work_bytes, const bsvd_opts* opts,      \
+    void* stream
+
+bsvd_status bsvd_sgesvj_strided(BSVD_STRIDED_ARGS(float, float));
+bsvd_status bsvd_dgesvj_strided(BSVD_STRIDED_ARGS(double, double));
+bsvd_status bsvd_cgesvj_strided(BSVD_STRIDED_ARGS(void, float));    /* T = complex float  */
+bsvd_status bsvd_zgesvj_strided(BSVD_STRIDED_ARGS(void, double));   /* T = complex double */
+
+/*
+ * Pointer-array batch (per-matrix shapes).  dA, dS, dU, dV are DEVICE arrays
+ * of `batch` device pointers (as in batched BLAS); m, n, lda, ldu, ldv are
+ * HOST arrays of `batch` ints.  Matrices are grouped by shape on the host and
+ * each group runs as one launch.  Arguments:
+ *   1 handle 2 jobu 3 jobv 4 batch 5 m[] 6 n[] 7 dA[] 8 lda[] 9 dS[]
+ *  10 dU[] 11 ldu[] 12 dV[] 13 ldv[] 14 d_info 15 d_sweeps 16 d_work
+ *  17 work_bytes 18 opts 19 stream
+ */
+#define BSVD_BATCHED_ARGS(T, R)                                                             \
+    bsvd_handle handle, bsvd_job jobu, bsvd_job jobv, int batch, const int* m, const int* n, \
+    const T* const* dA, const int* lda, R* const* dS, T* const* dU, const int* ldu,          \
+    T* const* dV, const int* ldv, int* d_info, int* d_sweeps, void* d_work,                  \
+    size_t work_bytes, const bsvd_opts* opts, void* stream
+
+bsvd_status bsvd_sgesvj_batched(BSVD_BATCHED_ARGS(float, float));
+bsvd_status bsvd_dgesvj_batched(BSVD_BATCHED_ARGS(double, double));
+bsvd_status bsvd_cgesvj_batched(BSVD_BATCHED_ARGS(void, float));
+bsvd_status bsvd_zgesvj_batched(BSVD_BATCHED_ARGS(void, double));
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSVD_H */

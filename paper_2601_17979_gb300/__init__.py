@@ -1,0 +1,18 @@
+"""Batched one-sided Jacobi SVD for NVIDIA GB300 (sm_103a).
+
+The method of Abdelfattah and Fasi, "An Efficient Batch Solver for the
+Singular Value Decomposition on GPUs": blocked one-sided Jacobi with one
+inner Jacobi sweep per Gram block, fused vector updates and per-matrix
+masking, as hand-written CUDA kernels behind the C-ABI of include/bsvd.h.
+
+    import paper_2601_17979_gb300 as bsvd
+    bsvd.build()                         # nvcc, once
+    res = bsvd.gesvj(A)                  # A: CUDA tensor (batch, m, n)
+    res.S, res.U, res.V, res.info, res.sweeps
+"""
+from .buildlib import build
+from .binding import (BsvdError, SVDResult, gesvj, gesvj_batched, load, handle, make_opts,
+                      column_major, empty_column_major, EXPORTS)
+
+__all__ = ["build", "BsvdError", "SVDResult", "gesvj", "gesvj_batched", "load", "handle",
+           "make_opts", "column_major", "empty_column_major", "EXPORTS"]

@@ -1,0 +1,238 @@
+"""Python binding of libbsvd (ctypes): argument marshalling only.
+
+Every step of the SVD runs in the CUDA kernels behind the C-ABI declared in
+``include/bsvd.h``; this module allocates outputs with torch, passes device
+pointers and the current CUDA stream, and checks status codes.  There is no
+CPU fallback: if the library is missing or no CUDA device is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from collections import namedtuple
+
+import torch
+
+from . import buildlib as _build
+
+BSVD_OK = 0
+STATUS = {0: "BSVD_OK", -1: "BSVD_ERR_INVALID", -2: "BSVD_ERR_WORKSPACE", -3: "BSVD_ERR_CUDA",
+          -4: "BSVD_ERR_TIMEOUT", -5: "BSVD_ERR_NOT_IMPLEMENTED", -6: "BSVD_ERR_NOMEM"}
+PATHS = {"auto": 0, "fused": 1, "plain": 2}
+DTYPES = {torch.float32: "s", torch.float64: "d", torch.complex64: "c", torch.complex128: "z"}
+REAL = {torch.float32: torch.float32, torch.float64: torch.float64,
+        torch.complex64: torch.float32, torch.complex128: torch.float64}
+
+SVDResult = namedtuple("SVDResult", "S U V info sweeps")
+
+EXPORTS = (
+    "bsvd_create", "bsvd_destroy", "bsvd_status_string", "bsvd_last_arg", "bsvd_last_cuda",
+    "bsvd_version", "bsvd_gesvj_workspace",
+    "bsvd_sgesvj_strided", "bsvd_dgesvj_strided", "bsvd_cgesvj_strided", "bsvd_zgesvj_strided",
+    "bsvd_sgesvj_batched", "bsvd_dgesvj_batched", "bsvd_cgesvj_batched", "bsvd_zgesvj_batched",
+)
+
+
+class BsvdError(RuntimeError):
+    def __init__(self, status: int, where: str, arg: int = 0, cuda: int = 0):
+        self.status, self.arg, self.cuda = status, arg, cuda
+        extra = f" (argument {arg})" if arg else ""
+        extra += f" (cudaError {cuda})" if status == -3 else ""
+        super().__init__(f"{where}: {STATUS.get(status, status)}{extra}")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("tol", ctypes.c_double),
+                ("inner_sweeps", ctypes.c_int), ("path", ctypes.c_int), ("flags", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
+
+
+_lock = threading.Lock()
+_lib = None
+_handle = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load libbsvd.so (built by ``build.build()``); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"{_build.LIB} is not built; run paper_2601_17979_gb300.build()")
+            L = ctypes.CDLL(_build.LIB)
+            P, I, LL, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_size_t
+            L.bsvd_create.argtypes = [ctypes.POINTER(P)]
+            L.bsvd_destroy.argtypes = [P]
+            L.bsvd_status_string.argtypes = [I]
+            L.bsvd_status_string.restype = ctypes.c_char_p
+            L.bsvd_last_arg.argtypes = [P]
+            L.bsvd_last_cuda.argtypes = [P]
+            L.bsvd_gesvj_workspace.argtypes = [P, ctypes.c_char, I, P, P, I, I, I, ctypes.POINTER(Opts),
+                                               ctypes.POINTER(SZ)]
+            for t in "sdcz":
+                getattr(L, f"bsvd_{t}gesvj_strided").argtypes = [
+                    P, I, I, I, I, I, P, I, LL, P, LL, P, I, LL, P, I, LL, P, P, P, SZ,
+                    ctypes.POINTER(Opts), P]
+                getattr(L, f"bsvd_{t}gesvj_batched").argtypes = [
+                    P, I, I, I, P, P, P, P, P, P, P, P, P, P, P, P, SZ, ctypes.POINTER(Opts), P]
+            _lib = L
+    return _lib
+
+
+def handle() -> ctypes.c_void_p:
+    global _handle
+    L = load()
+    with _lock:
+        if _handle is None:
+            h = ctypes.c_void_p()
+            st = L.bsvd_create(ctypes.byref(h))
+            if st != BSVD_OK:
+                raise BsvdError(st, "bsvd_create")
+            _handle = h
+    return _handle
+
+
+def _check(st: int, where: str):
+    if st != BSVD_OK:
+        L, h = load(), handle()
+        raise BsvdError(st, where, L.bsvd_last_arg(h), L.bsvd_last_cuda(h))
+
+
+def make_opts(nb=0, tol=0.0, max_sweeps=0, inner_sweeps=0, path="auto", flags=0) -> Opts:
+    o = Opts()
+    o.nb, o.tol, o.max_sweeps, o.inner_sweeps = int(nb), float(tol), int(max_sweeps), int(inner_sweeps)
+    o.path, o.flags = PATHS[path] if isinstance(path, str) else int(path), int(flags)
+    return o
+
+
+def _stream_ptr(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def column_major(A: torch.Tensor) -> torch.Tensor:
+    """(batch, m, n) view whose matrices are column-major (stride(-2) == 1)."""
+    if A.stride(-2) == 1 and (A.stride(-1) >= max(1, A.shape[-2]) or A.shape[-1] == 1):
+        return A
+    return A.transpose(-1, -2).contiguous().transpose(-1, -2)
+
+
+def leading_dim(X: torch.Tensor) -> int:
+    """Leading dimension of a column-major matrix view; a single column's
+    stride is meaningless (torch may report 1), so it is taken as the rows."""
+    rows = X.shape[-2]
+    if X.shape[-1] <= 1:
+        return max(1, rows)
+    return max(1, X.stride(-1))
+
+
+def empty_column_major(batch: int, rows: int, cols: int, dtype, device) -> torch.Tensor:
+    return torch.empty((batch, cols, rows), dtype=dtype, device=device).transpose(1, 2)
+
+
+def gesvj(A: torch.Tensor, compute_u: bool = True, compute_v: bool = True, *, nb: int = 0,
+          tol: float = 0.0, max_sweeps: int = 0, inner_sweeps: int = 0, path="auto",
+          flags: int = 0, out=None, stream=None) -> SVDResult:
+    """SVD of every matrix of a CUDA tensor A (batch, m, n) or (m, n).
+
+    A may be float32, float64, complex64 or complex128; matrices are read
+    column-major (a copy is made if A is not).  Returns S (batch, k), U
+    (batch, m, k), V (batch, n, k) with k = min(m, n) (U/V None when not
+    requested), and int32 info and sweeps (batch,).  ``out`` may pass
+    preallocated (S, U, V, info, sweeps) in that layout.
+    """
+    if A.dtype not in DTYPES:
+        raise TypeError(f"unsupported dtype {A.dtype}")
+    if not A.is_cuda:
+        raise ValueError("A must be a CUDA tensor")
+    squeeze = A.dim() == 2
+    if squeeze:
+        A = A.unsqueeze(0)
+    A = column_major(A)
+    batch, m, n = A.shape
+    k = min(m, n)
+    dev = A.device
+    if out is None:
+        S = torch.empty((batch, k), dtype=REAL[A.dtype], device=dev)
+        U = empty_column_major(batch, m, k, A.dtype, dev) if compute_u else None
+        V = empty_column_major(batch, n, k, A.dtype, dev) if compute_v else None
+        info = torch.empty(batch, dtype=torch.int32, device=dev)
+        sweeps = torch.empty(batch, dtype=torch.int32, device=dev)
+    else:
+        S, U, V, info, sweeps = out
+    o = make_opts(nb, tol, max_sweeps, inner_sweeps, path, flags)
+    t = DTYPES[A.dtype]
+    L = load()
+    f = getattr(L, f"bsvd_{t}gesvj_strided")
+    st = f(handle(), int(compute_u), int(compute_v), batch, m, n,
+           A.data_ptr(), leading_dim(A), A.stride(0),
+           S.data_ptr(), S.stride(0) if batch > 1 else k,
+           U.data_ptr() if U is not None else None, leading_dim(U) if U is not None else 1,
+           U.stride(0) if U is not None else 0,
+           V.data_ptr() if V is not None else None, leading_dim(V) if V is not None else 1,
+           V.stride(0) if V is not None else 0,
+           info.data_ptr(), sweeps.data_ptr() if sweeps is not None else None, None, 0,
+           ctypes.byref(o), _stream_ptr(stream))
+    _check(st, f"bsvd_{t}gesvj_strided")
+    if squeeze:
+        return SVDResult(S[0], U[0] if U is not None else None, V[0] if V is not None else None,
+                         info, sweeps)
+    return SVDResult(S, U, V, info, sweeps)
+
+
+def gesvj_batched(mats, compute_u: bool = True, compute_v: bool = True, *, nb: int = 0,
+                  tol: float = 0.0, max_sweeps: int = 0, inner_sweeps: int = 0, path="auto",
+                  flags: int = 0, stream=None):
+    """SVD of a list of CUDA matrices of any shapes (one dtype) through the
+    pointer-array entry point.  Returns lists S, U, V and info, sweeps."""
+    mats = [column_major(x) if x.dim() == 2 else None for x in mats]
+    if any(x is None for x in mats):
+        raise ValueError("every matrix must be 2-D")
+    dt = mats[0].dtype
+    if any(x.dtype != dt for x in mats) or dt not in DTYPES:
+        raise TypeError("all matrices must share one supported dtype")
+    dev = mats[0].device
+    B = len(mats)
+    ms = (ctypes.c_int * max(B, 1))(*[x.shape[0] for x in mats])
+    ns = (ctypes.c_int * max(B, 1))(*[x.shape[1] for x in mats])
+    lda = (ctypes.c_int * max(B, 1))(*[leading_dim(x) for x in mats])
+    S = [torch.empty(min(x.shape), dtype=REAL[dt], device=dev) for x in mats]
+    U = [torch.empty((min(x.shape), x.shape[0]), dtype=dt, device=dev).t() for x in mats] if compute_u else None
+    V = [torch.empty((min(x.shape), x.shape[1]), dtype=dt, device=dev).t() for x in mats] if compute_v else None
+    ldu = (ctypes.c_int * max(B, 1))(*[max(x.shape[0], 1) for x in mats])
+    ldv = (ctypes.c_int * max(B, 1))(*[max(x.shape[1], 1) for x in mats])
+
+    def ptrs(ts):
+        return torch.tensor([t.data_ptr() for t in ts], dtype=torch.int64, device=dev)
+
+    pA, pS = ptrs(mats), ptrs(S)
+    pU = ptrs(U) if U is not None else None
+    pV = ptrs(V) if V is not None else None
+    info = torch.empty(B, dtype=torch.int32, device=dev)
+    sweeps = torch.empty(B, dtype=torch.int32, device=dev)
+    o = make_opts(nb, tol, max_sweeps, inner_sweeps, path, flags)
+    L, h = load(), handle()
+    t = DTYPES[dt]
+    nbytes = ctypes.c_size_t()
+    _check(L.bsvd_gesvj_workspace(h, t.encode(), B, ctypes.cast(ms, ctypes.c_void_p),
+                                  ctypes.cast(ns, ctypes.c_void_p), 0, int(compute_u),
+                                  int(compute_v), ctypes.byref(o), ctypes.byref(nbytes)),
+           "bsvd_gesvj_workspace")
+    work = torch.empty(max(nbytes.value, 16), dtype=torch.uint8, device=dev)
+    f = getattr(L, f"bsvd_{t}gesvj_batched")
+    st = f(h, int(compute_u), int(compute_v), B, ctypes.cast(ms, ctypes.c_void_p),
+           ctypes.cast(ns, ctypes.c_void_p), pA.data_ptr(), ctypes.cast(lda, ctypes.c_void_p),
+           pS.data_ptr(), pU.data_ptr() if pU is not None else None,
+           ctypes.cast(ldu, ctypes.c_void_p), pV.data_ptr() if pV is not None else None,
+           ctypes.cast(ldv, ctypes.c_void_p), info.data_ptr(), sweeps.data_ptr(),
+           work.data_ptr(), work.numel(), ctypes.byref(o), _stream_ptr(stream))
+    _check(st, f"bsvd_{t}gesvj_batched")
+    # keep the pointer arrays and workspace alive until the kernels finish
+    torch.cuda.current_stream(dev).synchronize() if stream is None else stream.synchronize()
+    return SVDResult(S, U, V, info, sweeps)

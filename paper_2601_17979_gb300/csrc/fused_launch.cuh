@@ -1,0 +1,86 @@
+// fused_launch.cuh -- shared-memory planning and launch of the fused kernel,
+// instantiated once per scalar type by fused_{s,d,c,z}.cu.
+#pragma once
+
+#include "gesvj_fused.cuh"
+#include "internal.h"
+
+namespace bsvd {
+
+// Thread organisation per block width: NG groups of GT threads, one group
+// per block pair of a round-robin round.
+template <int NB> struct FusedCfg;
+template <> struct FusedCfg<4>  { static constexpr int NG = 2, GT = 32; };
+template <> struct FusedCfg<8>  { static constexpr int NG = 2, GT = 64; };
+template <> struct FusedCfg<16> { static constexpr int NG = 2, GT = 128; };
+
+inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+template <class T, int NB>
+size_t fused_plan_nb(int M, int N, bool needVs, FusedArgs& a, int& nthreads) {
+    using C = FusedCfg<NB>;
+    using R = Real<T>;
+    const int l = N > 2 * NB ? (N + NB - 1) / NB : 2;
+    a.l = l;
+    a.L = l + (l & 1);
+    a.Np = l * NB;
+    a.ldw = M | 1;
+    a.ldvs = N | 1;
+    a.lde = N | 1;
+    size_t off = 0;
+    a.offW = 0;
+    off = align16((size_t)a.ldw * a.Np * sizeof(T));
+    a.offV = (int)off;
+    if (needVs) off = align16(off + (size_t)a.ldvs * a.Np * sizeof(T));
+    a.offG = (int)off;
+    a.groupBytes = fused_group_bytes<T, NB>();
+    off += (size_t)C::NG * a.groupBytes;
+    a.offMisc = (int)off;
+    const int NT = C::NG * C::GT, NW = NT / 32;
+    off += kMaxSweeps * 4 + 16 + 2 * sizeof(T);
+    off += (size_t)((NW + 3) & ~3) * sizeof(R) + (size_t)((N + 3) & ~3) * sizeof(R) + (size_t)N * 4;
+    nthreads = NT;
+    return align16(off);
+}
+
+template <class T>
+size_t fused_plan(int nb, int M, int N, bool needVs, FusedArgs& a, int& nthreads) {
+    switch (nb) {
+        case 4: return fused_plan_nb<T, 4>(M, N, needVs, a, nthreads);
+        case 8: return fused_plan_nb<T, 8>(M, N, needVs, a, nthreads);
+        case 16: return fused_plan_nb<T, 16>(M, N, needVs, a, nthreads);
+        default: return 0;
+    }
+}
+
+template <class T, int NB>
+cudaError_t fused_launch_nb(const FusedArgs& a, int grid, size_t smem, cudaStream_t st) {
+    using C = FusedCfg<NB>;
+    auto k = gesvj_fused_kernel<T, NB, C::NG, C::GT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, C::NG * C::GT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t fused_launch(int nb, const FusedArgs& a, int grid, size_t smem, cudaStream_t st) {
+    switch (nb) {
+        case 4: return fused_launch_nb<T, 4>(a, grid, smem, st);
+        case 8: return fused_launch_nb<T, 8>(a, grid, smem, st);
+        case 16: return fused_launch_nb<T, 16>(a, grid, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace bsvd
+
+// One TU per type defines these with FUSED_TYPE / FUSED_TAG.
+#define BSVD_DEFINE_FUSED(TYPE, TAG)                                                           \
+    size_t bsvd::fused_plan_##TAG(int nb, int M, int N, bool needVs, FusedArgs& a, int& nt) { \
+        return fused_plan<TYPE>(nb, M, N, needVs, a, nt);                                    \
+    }                                                                                        \
+    cudaError_t bsvd::fused_launch_##TAG(int nb, const FusedArgs& a, int grid, size_t smem,  \
+                                         cudaStream_t st) {                                  \
+        return fused_launch<TYPE>(nb, a, grid, smem, st);                                    \
+    }

@@ -1,0 +1,115 @@
+"""The C-ABI library loads, exports every declared symbol, and rejects bad
+arguments on the host with the documented argument positions (no GPU needed:
+argument checks run before any CUDA call)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import __graft_entry__  # noqa: F401  (puts the repo root on sys.path)
+import paper_2601_17979_gb300 as bsvd
+from paper_2601_17979_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    bsvd.build()
+    return bsvd.load()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "bsvd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bsvd_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    syms = declared_symbols()
+    assert len(syms) >= 15
+    missing = [s for s in syms if not hasattr(L, s)]
+    assert missing == []
+    assert sorted(binding.EXPORTS) == syms
+
+
+def test_version_and_status_strings(L):
+    assert L.bsvd_version() == 1
+    for st in (0, -1, -2, -3, -4, -5, -6):
+        assert L.bsvd_status_string(st).startswith(b"BSVD_")
+
+
+def call_strided(L, t="d", **kw):
+    a = dict(jobu=1, jobv=1, batch=2, m=8, n=4, dA=16, lda=8, sA=32, dS=16, sS=4, dU=16, ldu=8,
+             sU=32, dV=16, ldv=4, sV=16, info=16, sweeps=None, work=None, wbytes=0)
+    a.update(kw)
+    o = binding.make_opts(**kw.get("opts", {}))
+    f = getattr(L, f"bsvd_{t}gesvj_strided")
+    return f(bsvd.handle(), a["jobu"], a["jobv"], a["batch"], a["m"], a["n"], a["dA"], a["lda"],
+             a["sA"], a["dS"], a["sS"], a["dU"], a["ldu"], a["sU"], a["dV"], a["ldv"], a["sV"],
+             a["info"], a["sweeps"], a["work"], a["wbytes"], ctypes.byref(o), None)
+
+
+@pytest.mark.parametrize("field,value,pos", [
+    ("jobu", 7, 2), ("jobv", -1, 3), ("batch", -1, 4), ("m", -2, 5), ("n", -1, 6),
+    ("dA", None, 7), ("lda", 7, 8), ("sA", 31, 9), ("dS", None, 10), ("sS", 3, 11),
+    ("dU", None, 12), ("ldu", 7, 13), ("sU", 31, 14), ("dV", None, 15), ("ldv", 3, 16),
+    ("sV", 15, 17), ("info", None, 18),
+])
+def test_strided_invalid_argument_positions(L, field, value, pos):
+    st = call_strided(L, **{field: value})
+    assert st == -1
+    assert L.bsvd_last_arg(bsvd.handle()) == pos
+
+
+def test_invalid_options(L):
+    assert call_strided(L, opts=dict(nb=-1)) == -1
+    assert L.bsvd_last_arg(bsvd.handle()) == 22
+
+
+def test_empty_batch_is_a_noop(L):
+    assert call_strided(L, batch=0, dA=None, dS=None, dU=None, dV=None, info=None) == 0
+
+
+def test_jobs_none_skip_vector_checks(L):
+    # with jobu = jobv = NONE the U/V pointers and leading dimensions are ignored
+    st = call_strided(L, jobu=0, jobv=0, dU=None, ldu=0, sU=0, dV=None, ldv=0, sV=0, batch=-3)
+    assert st == -1 and L.bsvd_last_arg(bsvd.handle()) == 4
+
+
+def test_workspace_query(L):
+    h = bsvd.handle()
+    n = ctypes.c_size_t(123)
+    m_arr = (ctypes.c_int * 3)(4, 5, 6)
+    o = binding.make_opts()
+    assert L.bsvd_gesvj_workspace(h, b"d", 3, m_arr, m_arr, 1, 1, 1, ctypes.byref(o), ctypes.byref(n)) == 0
+    assert n.value == 0
+    assert L.bsvd_gesvj_workspace(h, b"z", 3, m_arr, m_arr, 0, 1, 1, ctypes.byref(o), ctypes.byref(n)) == 0
+    assert n.value >= 4 * 3 * 4 and n.value % 256 == 0
+    assert L.bsvd_gesvj_workspace(h, b"q", 3, m_arr, m_arr, 0, 1, 1, ctypes.byref(o), ctypes.byref(n)) == -1
+    assert L.bsvd_last_arg(h) == 2
+
+
+def test_batched_invalid_arguments(L):
+    h = bsvd.handle()
+    B = 2
+    ms = (ctypes.c_int * B)(8, 6)
+    ns = (ctypes.c_int * B)(4, 6)
+    lda_bad = (ctypes.c_int * B)(8, 5)
+    ld = (ctypes.c_int * B)(8, 6)
+    o = binding.make_opts()
+    f = L.bsvd_dgesvj_batched
+    st = f(h, 1, 1, B, ms, ns, 16, lda_bad, 16, 16, ld, 16, ld, 16, None, 16, 4096, ctypes.byref(o), None)
+    assert st == -1 and L.bsvd_last_arg(h) == 8
+    # workspace too small
+    st = f(h, 1, 1, B, ms, ns, 16, ld, 16, 16, ld, 16, ns, 16, None, 16, 8, ctypes.byref(o), None)
+    assert st == -2
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # the binding never falls back to another implementation
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding._build, "LIB", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        binding.load()
