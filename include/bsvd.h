@@ -21,7 +21,9 @@
  *    call is asynchronous on `stream` (a cudaStream_t, NULL = legacy default
  *    stream) and returns after argument checks and kernel enqueue.
  *  - A is read only.  The caller owns every buffer, including the workspace;
- *    the library allocates no device memory.
+ *    the library allocates no device memory.  The on-chip (FUSED) path needs
+ *    no workspace for the strided form; the multi-kernel paths need
+ *    bsvd_gesvj_workspace() bytes (W, V, Gram and rotation blocks per matrix).
  *  - Status codes are synchronous (argument and launch errors).  On
  *    BSVD_ERR_INVALID, bsvd_last_arg() gives the 1-based position of the
  *    offending argument.  Per-matrix results go to d_info on the device:
@@ -59,11 +61,15 @@ typedef enum {
 typedef enum { BSVD_JOB_NONE = 0, BSVD_JOB_SOME = 1 } bsvd_job;   /* economy-size vectors */
 
 typedef enum {
-    BSVD_PATH_AUTO = 0,     /* fastest path that fits                                   */
-    BSVD_PATH_FUSED = 1,    /* one kernel per matrix, A and V resident on chip          */
-    BSVD_PATH_PLAIN = 2     /* the paper's baseline (Sec. 4): one launch per stage and
-                               round, inner eigensolver run to convergence, two-stage
-                               vector update, no masks; FP64 comparison path           */
+    BSVD_PATH_AUTO = 0,     /* FUSED when the matrix fits on chip, else BLOCKED          */
+    BSVD_PATH_FUSED = 1,    /* one kernel per matrix, A and V resident in shared memory  */
+    BSVD_PATH_PLAIN = 2,    /* the paper's baseline (Sec. 4): one launch per stage and
+                               round, inner eigensolver run to convergence (default 30
+                               inner sweeps), two-stage vector update, no masks, batch-
+                               level convergence checked on the host once per sweep (the
+                               call then synchronises `stream`); FP64 comparison path   */
+    BSVD_PATH_BLOCKED = 3   /* the multi-kernel path with Designs 2-4 (one inner sweep,
+                               fused update, masks); any matrix size; asynchronous      */
 } bsvd_path;
 
 /* Solver options.  Zero-initialise, then set what you need; 0 = default. */
@@ -74,7 +80,11 @@ typedef struct {
                           0 = 30 u, u the unit roundoff of the type (Sec. 5.4, k = 30)      */
     int inner_sweeps;  /* inner eigensolver sweeps per Gram block; 0 = 1 (Design-2, Sec. 5) */
     int path;          /* bsvd_path                                                         */
-    int flags;         /* bit 0: skip the final orthogonality correction of V              */
+    int flags;         /* bit 0: skip the final orthogonality correction of V;
+                          bit 1: two-stage vector update (Design-3 off; multi-kernel path);
+                          bit 2: no masks (Design-4 off; multi-kernel path, host-checked
+                          batch convergence).  Bits 1-2 with AUTO select the multi-kernel
+                          path.                                                              */
     int reserved[6];
 } bsvd_opts;
 
@@ -91,7 +101,9 @@ int bsvd_version(void);
  * Workspace query for one call.  dtype is 's', 'd', 'c' or 'z'.  For the
  * strided form pass m_arr = &m, n_arr = &n and uniform = 1; for the
  * pointer-array form pass the host arrays m[batch], n[batch] and uniform = 0.
- * *bytes receives the size of d_work the call needs (possibly 0).
+ * *bytes receives the size of d_work the call needs (possibly 0).  The query
+ * uses the current device's shared-memory limit to decide which shapes run
+ * on chip; with no CUDA device it assumes the GB300's 227 KB.
  */
 bsvd_status bsvd_gesvj_workspace(bsvd_handle handle, char dtype, int batch, const int* m_arr,
                                  const int* n_arr, int uniform, bsvd_job jobu, bsvd_job jobv,

@@ -12,7 +12,9 @@ masking, as hand-written CUDA kernels behind the C-ABI of include/bsvd.h.
 """
 from .buildlib import build
 from .binding import (BsvdError, SVDResult, gesvj, gesvj_batched, load, handle, make_opts,
-                      column_major, empty_column_major, EXPORTS)
+                      column_major, empty_column_major, workspace_bytes, EXPORTS,
+                      FLAG_NO_V_CORRECTION, FLAG_TWO_STAGE, FLAG_NO_MASKS)
 
 __all__ = ["build", "BsvdError", "SVDResult", "gesvj", "gesvj_batched", "load", "handle",
-           "make_opts", "column_major", "empty_column_major", "EXPORTS"]
+           "make_opts", "column_major", "empty_column_major", "workspace_bytes", "EXPORTS",
+           "FLAG_NO_V_CORRECTION", "FLAG_TWO_STAGE", "FLAG_NO_MASKS"]

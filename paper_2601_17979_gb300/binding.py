@@ -20,7 +20,8 @@ from . import buildlib as _build
 BSVD_OK = 0
 STATUS = {0: "BSVD_OK", -1: "BSVD_ERR_INVALID", -2: "BSVD_ERR_WORKSPACE", -3: "BSVD_ERR_CUDA",
           -4: "BSVD_ERR_TIMEOUT", -5: "BSVD_ERR_NOT_IMPLEMENTED", -6: "BSVD_ERR_NOMEM"}
-PATHS = {"auto": 0, "fused": 1, "plain": 2}
+PATHS = {"auto": 0, "fused": 1, "plain": 2, "blocked": 3}
+FLAG_NO_V_CORRECTION, FLAG_TWO_STAGE, FLAG_NO_MASKS = 1, 2, 4
 DTYPES = {torch.float32: "s", torch.float64: "d", torch.complex64: "c", torch.complex128: "z"}
 REAL = {torch.float32: torch.float32, torch.float64: torch.float64,
         torch.complex64: torch.float32, torch.complex128: torch.float64}
@@ -136,9 +137,25 @@ def empty_column_major(batch: int, rows: int, cols: int, dtype, device) -> torch
     return torch.empty((batch, cols, rows), dtype=dtype, device=device).transpose(1, 2)
 
 
+def workspace_bytes(dtype, shapes, uniform: bool, compute_u=True, compute_v=True, **opts) -> int:
+    """Device workspace (bytes) a call needs; shapes = [(m, n)] (uniform) or a list."""
+    L, h = load(), handle()
+    B = len(shapes) if not uniform else opts.pop("batch", 1)
+    ms = (ctypes.c_int * max(len(shapes), 1))(*[m for m, _ in shapes])
+    ns = (ctypes.c_int * max(len(shapes), 1))(*[n for _, n in shapes])
+    o = make_opts(**opts)
+    nbytes = ctypes.c_size_t()
+    t = DTYPES[dtype] if not isinstance(dtype, str) else dtype
+    _check(L.bsvd_gesvj_workspace(h, t.encode(), B, ctypes.cast(ms, ctypes.c_void_p),
+                                  ctypes.cast(ns, ctypes.c_void_p), int(uniform), int(compute_u),
+                                  int(compute_v), ctypes.byref(o), ctypes.byref(nbytes)),
+           "bsvd_gesvj_workspace")
+    return int(nbytes.value)
+
+
 def gesvj(A: torch.Tensor, compute_u: bool = True, compute_v: bool = True, *, nb: int = 0,
           tol: float = 0.0, max_sweeps: int = 0, inner_sweeps: int = 0, path="auto",
-          flags: int = 0, out=None, stream=None) -> SVDResult:
+          flags: int = 0, out=None, work=None, stream=None) -> SVDResult:
     """SVD of every matrix of a CUDA tensor A (batch, m, n) or (m, n).
 
     A may be float32, float64, complex64 or complex128; matrices are read
@@ -169,6 +186,11 @@ def gesvj(A: torch.Tensor, compute_u: bool = True, compute_v: bool = True, *, nb
     o = make_opts(nb, tol, max_sweeps, inner_sweeps, path, flags)
     t = DTYPES[A.dtype]
     L = load()
+    if work is None:
+        nbytes = workspace_bytes(A.dtype, [(m, n)], True, compute_u, compute_v, batch=batch, nb=nb,
+                                 tol=tol, max_sweeps=max_sweeps, inner_sweeps=inner_sweeps,
+                                 path=path, flags=flags)
+        work = torch.empty(nbytes, dtype=torch.uint8, device=dev) if nbytes else None
     f = getattr(L, f"bsvd_{t}gesvj_strided")
     st = f(handle(), int(compute_u), int(compute_v), batch, m, n,
            A.data_ptr(), leading_dim(A), A.stride(0),
@@ -177,7 +199,8 @@ def gesvj(A: torch.Tensor, compute_u: bool = True, compute_v: bool = True, *, nb
            U.stride(0) if U is not None else 0,
            V.data_ptr() if V is not None else None, leading_dim(V) if V is not None else 1,
            V.stride(0) if V is not None else 0,
-           info.data_ptr(), sweeps.data_ptr() if sweeps is not None else None, None, 0,
+           info.data_ptr(), sweeps.data_ptr() if sweeps is not None else None,
+           work.data_ptr() if work is not None else None, work.numel() if work is not None else 0,
            ctypes.byref(o), _stream_ptr(stream))
     _check(st, f"bsvd_{t}gesvj_strided")
     if squeeze:

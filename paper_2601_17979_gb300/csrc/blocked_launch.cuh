@@ -1,0 +1,100 @@
+// blocked_launch.cuh -- workspace planning and the host sweep loop of the
+// multi-kernel path, instantiated once per scalar type by blocked_{s,d,c,z}.cu.
+#pragma once
+
+#include <algorithm>
+
+#include "blocked_layout.h"
+#include "gesvj_blocked.cuh"
+#include "internal.h"
+
+namespace bsvd {
+
+template <int NB> struct BlkCfg;
+template <> struct BlkCfg<4>  { static constexpr int GT = 32; };
+template <> struct BlkCfg<8>  { static constexpr int GT = 64; };
+template <> struct BlkCfg<16> { static constexpr int GT = 128; };
+template <> struct BlkCfg<32> { static constexpr int GT = 256; };
+
+template <class T, int NB>
+cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stage, bool host_sync) {
+    using R = Real<T>;
+    constexpr int TWO = 2 * NB, GT = BlkCfg<NB>::GT, LDG = TWO + 1;
+    const BlkSizes z = blk_sizes(NB, a.M, a.N, two_stage);
+    a.l = z.l; a.L = z.L; a.Np = z.Np;
+    a.sW = z.W; a.sVw = z.V; a.sG = z.G; a.sJ = z.J; a.sT = z.T;
+    char* p = static_cast<char*>(work);
+    a.state = reinterpret_cast<int*>(p);       p += blk_align((size_t)a.count * 4 * sizeof(int));
+    a.pairflag = reinterpret_cast<int*>(p);    p += blk_align((size_t)a.count * (z.L / 2) * sizeof(int));
+    a.any_active = reinterpret_cast<int*>(p);  p += blk_align(sizeof(int));
+    T* base = reinterpret_cast<T*>(p);
+    a.W = base;  base += (size_t)a.count * z.W;
+    a.Vw = base; base += (size_t)a.count * z.V;
+    a.G = base;  base += (size_t)a.count * z.G;
+    a.J = base;  base += (size_t)a.count * z.J;
+    a.T = base;
+
+    cudaError_t e;
+    const int heevj_smem = 2 * TWO * LDG * (int)sizeof(T) + InnerTables<T, NB>::bytes();
+    e = cudaFuncSetAttribute(blk_heevj<T, NB, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, heevj_smem);
+    if (e != cudaSuccess) return e;
+    const int fin_smem = (kBlkThreads / 32) * (int)sizeof(R) + 16 + 2 * (int)sizeof(T) +
+                         a.N * ((int)sizeof(R) + 4) + 16;
+    e = cudaFuncSetAttribute(blk_finalize<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, fin_smem);
+    if (e != cudaSuccess) return e;
+
+    const int upd_smem = TWO * TWO * (int)sizeof(T);
+    e = cudaFuncSetAttribute(blk_update_fused<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, upd_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(blk_update_stage1<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, upd_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(blk_update_stage2<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, upd_smem);
+    if (e != cudaSuccess) return e;
+
+    blk_load<T><<<a.count, kBlkThreads, 0, st>>>(a);
+    const dim3 gpair(a.count, z.L / 2);
+    const dim3 gupd(a.count, z.L / 2, (a.M + a.N + kUpdRows - 1) / kUpdRows);
+    for (int sw = 0; sw < a.max_sweeps; ++sw) {
+        for (int r = 0; r < z.L - 1; ++r) {
+            blk_gram<T, NB><<<gpair, kBlkThreads, 0, st>>>(a, r);
+            blk_heevj<T, NB, GT><<<gpair, GT, heevj_smem, st>>>(a, r);
+            if (two_stage) {
+                blk_update_stage1<T, NB><<<gupd, kUpdRows, upd_smem, st>>>(a, r);
+                blk_update_stage2<T, NB><<<gupd, kUpdRows, upd_smem, st>>>(a, r);
+            } else {
+                blk_update_fused<T, NB><<<gupd, kUpdRows, upd_smem, st>>>(a, r);
+            }
+        }
+        if ((e = cudaMemsetAsync(a.any_active, 0, sizeof(int), st)) != cudaSuccess) return e;
+        blk_converge<<<(a.count + 127) / 128, 128, 0, st>>>(a);
+        if (host_sync) {
+            // batch-level convergence (the paper's unmasked design): stop once no
+            // matrix rotated in the last sweep
+            int any = 0;
+            if ((e = cudaMemcpyAsync(&any, a.any_active, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+            if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+            if (!any) break;
+        }
+    }
+    blk_finalize<T><<<a.count, kBlkThreads, fin_smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t blk_run(int nb, const BlockedArgs& a, void* work, cudaStream_t st, bool two_stage, bool host_sync) {
+    switch (nb) {
+        case 4: return blk_run_nb<T, 4>(a, work, st, two_stage, host_sync);
+        case 8: return blk_run_nb<T, 8>(a, work, st, two_stage, host_sync);
+        case 16: return blk_run_nb<T, 16>(a, work, st, two_stage, host_sync);
+        case 32: return blk_run_nb<T, 32>(a, work, st, two_stage, host_sync);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace bsvd
+
+#define BSVD_DEFINE_BLOCKED(TYPE, TAG)                                                          \
+    cudaError_t bsvd::blocked_run_##TAG(int nb, const BlockedArgs& a, void* work, cudaStream_t st, \
+                                        bool two_stage, bool host_sync) {                       \
+        return blk_run<TYPE>(nb, a, work, st, two_stage, host_sync);                            \
+    }

@@ -1,0 +1,68 @@
+// blocked_layout.h -- arguments and per-matrix workspace layout of the
+// multi-kernel path (shared by the C-ABI layer and the kernel launcher).
+#pragma once
+
+#include <stddef.h>
+
+#include <algorithm>
+
+namespace bsvd {
+
+// Arguments of the multi-kernel path (type-erased pointers).
+struct BlockedArgs {
+    int M, N, trans, m, n;     // working shape (M >= N) and the caller's
+    int l, L, Np;              // blocks (l >= 2), L = l + (l odd), Np = l * nb
+    int count;                 // matrices in this launch group
+    // workspace, per matrix: W (M x Np, ld M), Vw (N x Np, ld N), G and J
+    // (L/2 blocks of 2nb x 2nb), T (L/2 x (M+N) x 2nb two-stage temporary,
+    // also the finalisation scratch: >= N*N + M elements)
+    void* W; void* Vw; void* G; void* J; void* T;
+    long long sW, sVw, sG, sJ, sT;
+    int* state;                // count x 4: status (1 active, 0 converged, -1 bad), rotated, sweeps, exponent
+    int* pairflag;             // count x L/2: the pair rotated in this round
+    int* any_active;           // one int: some matrix still active after a sweep
+    // caller's arrays (as FusedArgs)
+    const void* A; long long sA; int lda; const void* const* Ap; const int* ldap;
+    void* S; long long sS; void* const* Sp;
+    void* U; long long sU; int ldu; void* const* Up; const int* ldup;
+    void* V; long long sV; int ldv; void* const* Vp; const int* ldvp;
+    const int* index;
+    int* info; int* sweeps;
+    double tol;
+    int max_sweeps, inner_sweeps, flags;
+    int masks;                 // Design-4
+    int wantU, wantV;
+};
+
+inline size_t blk_align(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Per-matrix element counts of each workspace region.
+struct BlkSizes {
+    long long W, V, G, J, T;
+    int l, L, Np;
+};
+
+inline BlkSizes blk_sizes(int nb, int M, int N, bool two_stage) {
+    BlkSizes z;
+    z.l = std::max(2, (N + nb - 1) / nb);
+    z.L = z.l + (z.l & 1);
+    z.Np = z.l * nb;
+    const long long two = 2LL * nb, pairs = z.L / 2;
+    z.W = (long long)M * z.Np;
+    z.V = (long long)N * z.Np;
+    z.G = pairs * two * two;
+    z.J = z.G;
+    const long long fin = (long long)M + (long long)N * N;           // finalisation scratch
+    z.T = std::max(two_stage ? pairs * (M + N) * two : 0LL, fin);
+    return z;
+}
+
+inline size_t blk_bytes(int nb, int M, int N, int count, bool two_stage, size_t elt) {
+    const BlkSizes z = blk_sizes(nb, M, N, two_stage);
+    size_t b = blk_align((size_t)count * 4 * sizeof(int)) + blk_align((size_t)count * (z.L / 2) * sizeof(int)) +
+               blk_align(sizeof(int));
+    b += blk_align((size_t)count * (z.W + z.V + z.G + z.J + z.T) * elt);
+    return b;
+}
+
+}  // namespace bsvd

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "bsvd.h"
+#include "blocked_layout.h"
 #include "gesvj_fused.cuh"
 #include "internal.h"
 
@@ -27,7 +28,9 @@ struct bsvd_handle_s {
 
 namespace {
 
+using bsvd::BlockedArgs;
 using bsvd::FusedArgs;
+using bsvd::blk_bytes;
 
 constexpr double kU32 = 5.9604644775390625e-08;     // 2^-24
 constexpr double kU64 = 1.1102230246251565e-16;     // 2^-53
@@ -68,72 +71,111 @@ bool resolve(const bsvd_opts* o, bool single, int N, Resolved& r) {
     std::memset(&z, 0, sizeof z);
     if (!o) o = &z;
     if (o->nb < 0 || o->max_sweeps < 0 || o->inner_sweeps < 0 || o->tol < 0 || o->path < 0 ||
-        o->path > BSVD_PATH_PLAIN)
+        o->path > BSVD_PATH_BLOCKED || o->flags < 0 || o->flags > 7)
         return false;
     r.nb = o->nb ? o->nb : (N >= 48 ? 16 : (N >= 12 ? 8 : 4));
     r.max_sweeps = o->max_sweeps ? o->max_sweeps : kDefaultMaxSweeps;
     r.max_sweeps = std::min(r.max_sweeps, bsvd::kMaxSweeps);
-    r.inner_sweeps = o->inner_sweeps ? o->inner_sweeps : 1;
-    r.tol = o->tol > 0 ? o->tol : 30.0 * (single ? kU32 : kU64);
     r.path = o->path;
+    r.inner_sweeps = o->inner_sweeps ? o->inner_sweeps : (r.path == BSVD_PATH_PLAIN ? 30 : 1);
+    r.tol = o->tol > 0 ? o->tol : 30.0 * (single ? kU32 : kU64);
     r.flags = o->flags;
     return true;
 }
 
 typedef size_t (*plan_fn)(int, int, int, bool, FusedArgs&, int&);
 typedef cudaError_t (*launch_fn)(int, const FusedArgs&, int, size_t, cudaStream_t);
+typedef cudaError_t (*blocked_fn)(int, const BlockedArgs&, void*, cudaStream_t, bool, bool);
 
 struct TypeOps {
     bool single;
     size_t elt;
     plan_fn plan;
     launch_fn launch;
+    blocked_fn blocked;
 };
 
 TypeOps ops_for(char t) {
     switch (t) {
-        case 's': return {true, 4, bsvd::fused_plan_s, bsvd::fused_launch_s};
-        case 'd': return {false, 8, bsvd::fused_plan_d, bsvd::fused_launch_d};
-        case 'c': return {true, 8, bsvd::fused_plan_c, bsvd::fused_launch_c};
-        default:  return {false, 16, bsvd::fused_plan_z, bsvd::fused_launch_z};
+        case 's': return {true, 4, bsvd::fused_plan_s, bsvd::fused_launch_s, bsvd::blocked_run_s};
+        case 'd': return {false, 8, bsvd::fused_plan_d, bsvd::fused_launch_d, bsvd::blocked_run_d};
+        case 'c': return {true, 8, bsvd::fused_plan_c, bsvd::fused_launch_c, bsvd::blocked_run_c};
+        default:  return {false, 16, bsvd::fused_plan_z, bsvd::fused_launch_z, bsvd::blocked_run_z};
     }
 }
 
-// One group of equal-shape matrices, planned for the fused kernel.
+// How one group of equal-shape matrices runs.
 struct Plan {
-    FusedArgs a;
+    bool blocked = false;
+    FusedArgs a;               // fused path
     size_t smem = 0;
     int threads = 0;
     int nb = 0;
+    bool two_stage = false, masks = true, host_sync = false;
+    size_t bytes = 0;          // workspace of the multi-kernel path
 };
 
-bsvd_status plan_group(bsvd_handle h, const TypeOps& ops, int m, int n, bool wantU, bool wantV,
-                       const Resolved& r, Plan& p) {
+bool fused_nb(int nb) { return nb == 4 || nb == 8 || nb == 16; }
+bool blocked_nb(int nb) { return nb == 4 || nb == 8 || nb == 16 || nb == 32; }
+
+bsvd_status plan_group(int max_smem, const TypeOps& ops, int m, int n, int count, bool wantU,
+                       bool wantV, const Resolved& r, Plan& p) {
     std::memset(&p.a, 0, sizeof p.a);
-    FusedArgs& a = p.a;
-    a.m = m;
-    a.n = n;
-    a.trans = m < n;
-    a.M = std::max(m, n);
-    a.N = std::min(m, n);
-    a.wantU = wantU;
-    a.wantV = wantV;
-    a.tol = r.tol;
-    a.max_sweeps = r.max_sweeps;
-    a.inner_sweeps = r.inner_sweeps;
-    a.flags = r.flags;
-    const bool needVs = a.trans ? wantU : wantV;
-    if (r.path == BSVD_PATH_PLAIN) return BSVD_ERR_NOT_IMPLEMENTED;
+    const int M = std::max(m, n), N = std::min(m, n);
+    const bool needVs = (m < n) ? wantU : wantV;
     p.nb = r.nb;
-    p.smem = ops.plan(r.nb, a.M, a.N, needVs, a, p.threads);
-    if (p.smem == 0) return BSVD_ERR_NOT_IMPLEMENTED;       // unsupported nb
-    if (p.smem > (size_t)h->max_smem) return BSVD_ERR_NOT_IMPLEMENTED;   // does not fit on chip
+    p.blocked = false;
+    const bool want_blocked_opts = (r.flags & 6) != 0;
+    if (r.path == BSVD_PATH_FUSED || (r.path == BSVD_PATH_AUTO && !want_blocked_opts)) {
+        if (fused_nb(r.nb)) {
+            p.smem = ops.plan(r.nb, M, N, needVs, p.a, p.threads);
+            if (p.smem > 0 && p.smem <= (size_t)max_smem) {
+                FusedArgs& a = p.a;
+                a.m = m; a.n = n; a.trans = m < n; a.M = M; a.N = N;
+                a.wantU = wantU; a.wantV = wantV;
+                a.tol = r.tol; a.max_sweeps = r.max_sweeps; a.inner_sweeps = r.inner_sweeps;
+                a.flags = r.flags;
+                return BSVD_OK;
+            }
+        }
+        if (r.path == BSVD_PATH_FUSED) return BSVD_ERR_NOT_IMPLEMENTED;   // does not fit on chip
+    }
+    if (!blocked_nb(r.nb)) return BSVD_ERR_NOT_IMPLEMENTED;
+    p.blocked = true;
+    p.two_stage = r.path == BSVD_PATH_PLAIN || (r.flags & 2);
+    p.masks = !(r.path == BSVD_PATH_PLAIN || (r.flags & 4));
+    p.host_sync = !p.masks;
+    p.bytes = bsvd::blocked_bytes(r.nb, M, N, count, p.two_stage, ops.elt);
     return BSVD_OK;
 }
 
-// Workspace of the pointer-array form: lda, ldu, ldv (3 x batch ints) plus
-// the matrix ids grouped by shape (batch ints).
-size_t batched_ws(int batch) { return ((size_t)4 * batch * sizeof(int) + 255) & ~size_t(255); }
+BlockedArgs blocked_args(int m, int n, int count, bool wantU, bool wantV, const Resolved& r, bool masks) {
+    BlockedArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.m = m; a.n = n; a.trans = m < n; a.M = std::max(m, n); a.N = std::min(m, n);
+    a.count = count;
+    a.wantU = wantU; a.wantV = wantV;
+    a.tol = r.tol; a.max_sweeps = r.max_sweeps; a.inner_sweeps = r.inner_sweeps;
+    a.flags = r.flags; a.masks = masks;
+    return a;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Workspace of the pointer-array form: lda, ldu, ldv (3 x batch ints) and the
+// matrix ids grouped by shape (batch ints), then each multi-kernel group's
+// region in shape order.
+size_t batched_ints(int batch) { return align256((size_t)4 * batch * sizeof(int)); }
+
+int device_smem_or_default(bsvd_handle h) {
+    int dev = 0, v = 0;
+    if (h->device >= 0) return h->max_smem;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess)
+        return v;
+    cudaGetLastError();
+    return 232448;   // GB300: 227 KB opt-in shared memory per block
+}
 
 bsvd_status strided_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, int batch, int m,
                          int n, const void* dA, int lda, long long sA, void* dS, long long sS,
@@ -161,8 +203,7 @@ bsvd_status strided_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
     if (wantV && ldv < std::max(1, n)) return fail_arg(h, 16);
     if (wantV && batch > 1 && sV < (long long)ldv * k) return fail_arg(h, 17);
     if (batch > 0 && !d_info) return fail_arg(h, 18);
-    (void)d_work;
-    (void)work_bytes;
+    if (d_work && (reinterpret_cast<uintptr_t>(d_work) & 15) != 0) return fail_arg(h, 20);
     const TypeOps ops = ops_for(t);
     Resolved r;
     if (!resolve(opts, ops.single, k, r)) return fail_arg(h, 22);
@@ -176,8 +217,20 @@ bsvd_status strided_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
         return e == cudaSuccess ? BSVD_OK : fail_cuda(h, e);
     }
     Plan p;
-    st = plan_group(h, ops, m, n, wantU, wantV, r, p);
+    st = plan_group(h->max_smem, ops, m, n, batch, wantU, wantV, r, p);
     if (st != BSVD_OK) return st;
+    if (p.blocked) {
+        if (!d_work || work_bytes < p.bytes) return BSVD_ERR_WORKSPACE;
+        BlockedArgs a = blocked_args(m, n, batch, wantU, wantV, r, p.masks);
+        a.A = dA; a.sA = sA; a.lda = lda;
+        a.S = dS; a.sS = sS;
+        a.U = dU; a.sU = sU; a.ldu = ldu;
+        a.V = dV; a.sV = sV; a.ldv = ldv;
+        a.info = d_info;
+        a.sweeps = d_sweeps;
+        cudaError_t e = ops.blocked(p.nb, a, d_work, s, p.two_stage, p.host_sync);
+        return e == cudaSuccess ? BSVD_OK : fail_cuda(h, e);
+    }
     FusedArgs& a = p.a;
     a.A = dA; a.sA = sA; a.lda = lda;
     a.S = dS; a.sS = sS;
@@ -187,6 +240,30 @@ bsvd_status strided_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
     a.sweeps = d_sweeps;
     cudaError_t e = ops.launch(p.nb, a, batch, p.smem, s);
     return e == cudaSuccess ? BSVD_OK : fail_cuda(h, e);
+}
+
+// Shape groups of a pointer-array batch, in a fixed order.
+using Groups = std::map<std::pair<int, int>, std::vector<int>>;
+
+bsvd_status plan_batched(int max_smem, const TypeOps& ops, int batch, const Groups& groups,
+                         bool wantU, bool wantV, const bsvd_opts* opts, std::vector<Plan>& plans,
+                         std::vector<Resolved>& res, size_t& total) {
+    total = batched_ints(batch);
+    plans.assign(groups.size(), Plan());
+    res.assign(groups.size(), Resolved());
+    size_t gi = 0;
+    for (auto& kv : groups) {
+        const int mm = kv.first.first, nn = kv.first.second;
+        if (!resolve(opts, ops.single, std::min(mm, nn), res[gi])) return BSVD_ERR_INVALID;
+        if (std::min(mm, nn) > 0) {
+            bsvd_status st = plan_group(max_smem, ops, mm, nn, (int)kv.second.size(), wantU, wantV,
+                                        res[gi], plans[gi]);
+            if (st != BSVD_OK) return st;
+            if (plans[gi].blocked) total += align256(plans[gi].bytes);
+        }
+        ++gi;
+    }
+    return BSVD_OK;
 }
 
 bsvd_status batched_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, int batch,
@@ -216,56 +293,49 @@ bsvd_status batched_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
         if (wantU && ldu[i] < std::max(1, m[i])) return fail_arg(h, 11);
         if (wantV && ldv[i] < std::max(1, n[i])) return fail_arg(h, 13);
     }
-    const size_t need = batched_ws(batch);
-    if (!d_work && work_bytes > 0) return fail_arg(h, 16);
-    if (work_bytes < need || !d_work) return BSVD_ERR_WORKSPACE;
-    if ((reinterpret_cast<uintptr_t>(d_work) & 15) != 0) return fail_arg(h, 16);
+    if (d_work && (reinterpret_cast<uintptr_t>(d_work) & 15) != 0) return fail_arg(h, 16);
     const TypeOps ops = ops_for(t);
-    bsvd_status st = refresh_device(h);
+    Groups groups;
+    for (int i = 0; i < batch; ++i) groups[{m[i], n[i]}].push_back(i);
+    // plan every group before touching the device, so a bad shape fails cleanly
+    std::vector<Plan> plans;
+    std::vector<Resolved> res;
+    size_t need = 0;
+    bsvd_status st = plan_batched(device_smem_or_default(h), ops, batch, groups, wantU, wantV, opts,
+                                  plans, res, need);
+    if (st == BSVD_ERR_INVALID) return fail_arg(h, 18);
+    if (st != BSVD_OK) return st;
+    if (!d_work || work_bytes < need) return BSVD_ERR_WORKSPACE;
+    st = refresh_device(h);
     if (st != BSVD_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-    // group matrix ids by shape
-    std::map<std::pair<int, int>, std::vector<int>> groups;
-    for (int i = 0; i < batch; ++i) groups[{m[i], n[i]}].push_back(i);
     std::vector<int> host((size_t)4 * batch);
     std::memcpy(host.data(), lda, sizeof(int) * batch);
     for (int i = 0; i < batch; ++i) {
         host[batch + i] = wantU ? ldu[i] : 1;
         host[2 * batch + i] = wantV ? ldv[i] : 1;
     }
+    std::vector<size_t> ipos;
     size_t pos = 3 * (size_t)batch;
-    std::vector<std::pair<size_t, const std::vector<int>*>> order;
     for (auto& kv : groups) {
-        order.push_back({pos, &kv.second});
+        ipos.push_back(pos);
         std::copy(kv.second.begin(), kv.second.end(), host.begin() + pos);
         pos += kv.second.size();
-    }
-    // plan every group before touching the device, so a bad shape fails cleanly
-    std::vector<Plan> plans(groups.size());
-    size_t gi = 0;
-    for (auto& kv : groups) {
-        const int mm = kv.first.first, nn = kv.first.second;
-        Resolved r;
-        if (!resolve(opts, ops.single, std::min(mm, nn), r)) return fail_arg(h, 18);
-        if (std::min(mm, nn) > 0) {
-            st = plan_group(h, ops, mm, nn, wantU, wantV, r, plans[gi]);
-            if (st != BSVD_OK) return st;
-        }
-        ++gi;
     }
     int* dws = static_cast<int*>(d_work);
     cudaError_t e = cudaMemcpyAsync(dws, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail_cuda(h, e);
-    gi = 0;
+    char* region = static_cast<char*>(d_work) + batched_ints(batch);
+    size_t gi = 0;
     for (auto& kv : groups) {
         const int mm = kv.first.first, nn = kv.first.second;
         const int count = (int)kv.second.size();
-        const size_t ipos = order[gi].first;
-        Plan& p = plans[gi++];
+        Plan& p = plans[gi];
+        const Resolved& r = res[gi];
+        const int* index = dws + ipos[gi];
+        ++gi;
         if (std::min(mm, nn) == 0) {
-            // zero-size matrices: info = 0 (written by a tiny memset per id is
-            // awkward; set through the fused kernel's tail instead is overkill)
             for (int id : kv.second) {
                 e = cudaMemsetAsync(d_info + id, 0, sizeof(int), s);
                 if (e == cudaSuccess && d_sweeps) e = cudaMemsetAsync(d_sweeps + id, 0, sizeof(int), s);
@@ -273,21 +343,38 @@ bsvd_status batched_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
             }
             continue;
         }
-        FusedArgs& a = p.a;
-        a.Ap = dA; a.ldap = dws;
-        a.Sp = dS;
-        a.Up = dU; a.ldup = dws + batch;
-        a.Vp = dV; a.ldvp = dws + 2 * batch;
-        a.index = dws + ipos;
-        a.info = d_info;
-        a.sweeps = d_sweeps;
-        e = ops.launch(p.nb, a, count, p.smem, s);
+        if (p.blocked) {
+            BlockedArgs a = blocked_args(mm, nn, count, wantU, wantV, r, p.masks);
+            a.Ap = dA; a.ldap = dws;
+            a.Sp = dS;
+            a.Up = dU; a.ldup = dws + batch;
+            a.Vp = dV; a.ldvp = dws + 2 * batch;
+            a.index = index;
+            a.info = d_info;
+            a.sweeps = d_sweeps;
+            e = ops.blocked(p.nb, a, region, s, p.two_stage, p.host_sync);
+            region += align256(p.bytes);
+        } else {
+            FusedArgs& a = p.a;
+            a.Ap = dA; a.ldap = dws;
+            a.Sp = dS;
+            a.Up = dU; a.ldup = dws + batch;
+            a.Vp = dV; a.ldvp = dws + 2 * batch;
+            a.index = index;
+            a.info = d_info;
+            a.sweeps = d_sweeps;
+            e = ops.launch(p.nb, a, count, p.smem, s);
+        }
         if (e != cudaSuccess) return fail_cuda(h, e);
     }
     return BSVD_OK;
 }
 
 }  // namespace
+
+size_t bsvd::blocked_bytes(int nb, int M, int N, int count, bool two_stage, size_t elt) {
+    return blk_bytes(nb, M, N, count, two_stage, elt);
+}
 
 extern "C" {
 
@@ -328,11 +415,35 @@ bsvd_status bsvd_gesvj_workspace(bsvd_handle handle, char dtype, int batch, cons
     if (batch < 0) return fail_arg(handle, 3);
     if (batch > 0 && (!m_arr || !n_arr)) return fail_arg(handle, !m_arr ? 4 : 5);
     if (!bytes) return fail_arg(handle, 10);
-    (void)jobu;
-    (void)jobv;
-    (void)opts;
-    *bytes = (uniform || batch == 0) ? 0 : batched_ws(batch);
-    return BSVD_OK;
+    *bytes = 0;
+    if (batch == 0) return BSVD_OK;
+    const TypeOps ops = ops_for(dtype);
+    const bool wantU = jobu == BSVD_JOB_SOME, wantV = jobv == BSVD_JOB_SOME;
+    const int max_smem = device_smem_or_default(handle);
+    if (uniform) {
+        const int m = m_arr[0], n = n_arr[0];
+        if (m < 0) return fail_arg(handle, 4);
+        if (n < 0) return fail_arg(handle, 5);
+        if (std::min(m, n) == 0) return BSVD_OK;
+        Resolved r;
+        if (!resolve(opts, ops.single, std::min(m, n), r)) return fail_arg(handle, 9);
+        Plan p;
+        bsvd_status st = plan_group(max_smem, ops, m, n, batch, wantU, wantV, r, p);
+        if (st != BSVD_OK) return st;
+        *bytes = p.blocked ? p.bytes : 0;
+        return BSVD_OK;
+    }
+    Groups groups;
+    for (int i = 0; i < batch; ++i) {
+        if (m_arr[i] < 0) return fail_arg(handle, 4);
+        if (n_arr[i] < 0) return fail_arg(handle, 5);
+        groups[{m_arr[i], n_arr[i]}].push_back(i);
+    }
+    std::vector<Plan> plans;
+    std::vector<Resolved> res;
+    bsvd_status st = plan_batched(max_smem, ops, batch, groups, wantU, wantV, opts, plans, res, *bytes);
+    if (st == BSVD_ERR_INVALID) return fail_arg(handle, 9);
+    return st;
 }
 
 #define BSVD_STRIDED_IMPL(TAG, T, R)                                                          \

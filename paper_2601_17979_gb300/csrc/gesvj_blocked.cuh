@@ -1,0 +1,343 @@
+// gesvj_blocked.cuh -- the multi-kernel blocked one-sided Jacobi SVD.
+//
+// The structure of Sec. 4: per round of the round-robin ordering, one launch
+// per stage over all (block pair, matrix) items, with the working matrix W,
+// V, the Gram blocks G and the eigenvector blocks J in a global-memory
+// workspace.  Options select the paper's design ladder:
+//   baseline (Sec. 4)  inner eigensolver run to convergence, two-stage
+//                      vector update through a temporary, no masks, the
+//                      batch converges when every matrix has (host check
+//                      once per sweep);
+//   Design-2 (Sec. 5)  one inner sweep;
+//   Design-3 (Sec. 6)  fused vector update (Alg. 4): one read, one write;
+//   Design-4 (Sec. 7)  masks: converged matrices and pairs whose J = I skip
+//                      the eigensolver and the update.
+// The same kernels serve any matrix too large for the on-chip fused path.
+#pragma once
+
+#include "blocked_layout.h"
+#include "jacobi_common.cuh"
+
+namespace bsvd {
+
+enum : int { kBlkThreads = 256, kUpdRows = 128, kGramChunk = 64 };
+
+__device__ __forceinline__ int blk_mid(const BlockedArgs& a, int b) { return a.index ? a.index[b] : b; }
+
+// skip this matrix? (bad input always; converged ones only with masks)
+__device__ __forceinline__ bool blk_skip(const BlockedArgs& a, int b) {
+    const int st = a.state[4 * b];
+    return st < 0 || (a.masks && st == 0);
+}
+
+// ---- load: W = A * 2^-ex (or A^H), padded; V = I; status -------------------
+template <class T>
+__global__ void __launch_bounds__(kBlkThreads) blk_load(const BlockedArgs a) {
+    using R = Real<T>;
+    constexpr int NT = kBlkThreads, NW = NT / 32;
+    __shared__ R red[NW];
+    __shared__ int bad_s, ex_s;
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int mid = blk_mid(a, b);
+    const T* A = a.Ap ? static_cast<const T*>(a.Ap[mid]) : static_cast<const T*>(a.A) + (long long)mid * a.sA;
+    const int lda = a.ldap ? a.ldap[mid] : a.lda;
+    R mx = 0;
+    int nonfin = 0;
+    for (int e = tid; e < a.m * a.n; e += NT) {
+        const T x = A[(e % a.m) + (long long)(e / a.m) * lda];
+        if (!finite_s(x)) nonfin = 1; else mx = fmax(mx, maxabs(x));
+    }
+    mx = warp_max(mx);
+    const bool wbad = __any_sync(0xffffffffu, nonfin);
+    if (lane == 0) red[warp] = wbad ? R(-1) : mx;
+    __syncthreads();
+    if (tid == 0) {
+        R m2 = 0;
+        int bd = 0;
+        for (int w = 0; w < NW; ++w) { bd |= red[w] < 0; m2 = fmax(m2, red[w]); }
+        bad_s = bd;
+        ex_s = (m2 > 0) ? ilogb_r(m2) : 0;
+        a.state[4 * b + 0] = bd ? -1 : 1;
+        a.state[4 * b + 1] = 0;
+        a.state[4 * b + 2] = 0;
+        a.state[4 * b + 3] = ex_s;
+    }
+    __syncthreads();
+    if (bad_s) return;
+    const int ex = ex_s;
+    T* W = static_cast<T*>(a.W) + b * a.sW;
+    T* V = static_cast<T*>(a.Vw) + b * a.sVw;
+    const int M = a.M, N = a.N;
+    for (int e = tid; e < a.m * a.n; e += NT) {
+        const int i = e % a.m, j = e / a.m;
+        const T x = scalb_s(A[i + (long long)j * lda], -ex);
+        if (a.trans) W[j + (long long)i * M] = conj_s(x);
+        else         W[i + (long long)j * M] = x;
+    }
+    for (int e = tid; e < M * (a.Np - N); e += NT) W[(e % M) + (long long)(N + e / M) * M] = make_s<T>(0);
+    for (int e = tid; e < N * a.Np; e += NT) V[(e % N) + (long long)(e / N) * N] = make_s<T>((e % N) == (e / N) ? 1 : 0);
+}
+
+// ---- S2: G = [A_i A_j]^H [A_i A_j] as three nb x nb products -----------------
+// (A_i^H A_i, A_j^H A_i, A_j^H A_j; Sec. 4.2) accumulated over chunks of rows
+// staged in shared memory.  grid (count, L/2).
+template <class T, int NB>
+__global__ void __launch_bounds__(kBlkThreads) blk_gram(const BlockedArgs a, int r) {
+    constexpr int TWO = 2 * NB, NT = kBlkThreads;
+    // rows per staged chunk: kGramChunk, fewer when the 2nb-wide tile would pass 32 KB
+    constexpr int KC = (kGramChunk * TWO * (int)sizeof(T) <= 32768) ? kGramChunk
+                                                                   : 32768 / (TWO * (int)sizeof(T));
+    constexpr int NE = 3 * NB * NB, PER = (NE + NT - 1) / NT;
+    __shared__ T P[KC * TWO];
+    const int b = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
+    if (blk_skip(a, b)) return;
+    int bi, bj;
+    rr_pair(a.L, r, q, bi, bj);
+    if (bj >= a.l) return;
+    const T* W = static_cast<const T*>(a.W) + b * a.sW;
+    const int M = a.M;
+    T acc[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) acc[u] = make_s<T>(0);
+    for (int k0 = 0; k0 < M; k0 += KC) {
+        const int kc = min(KC, M - k0);
+        for (int e = tid; e < KC * TWO; e += NT) {
+            const int kk = e % KC, c = e / KC;
+            const int col = c < NB ? bi * NB + c : bj * NB + (c - NB);
+            P[kk + c * KC] = kk < kc ? W[k0 + kk + (long long)col * M] : make_s<T>(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int e = tid + u * NT;
+            if (e < NE) {
+                const int blk = e / (NB * NB), w = e % (NB * NB), ra = w % NB, cb = w / NB;
+                const int row = (blk == 0) ? ra : NB + ra;      // (i,i), (j,i), (j,j)
+                const int col = (blk == 2) ? NB + cb : cb;
+                T s = acc[u];
+                for (int kk = 0; kk < kc; ++kk) s = cfma(P[kk + row * KC], P[kk + col * KC], s);
+                acc[u] = s;
+            }
+        }
+        __syncthreads();
+    }
+    T* G = static_cast<T*>(a.G) + b * a.sG + (long long)q * TWO * TWO;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int e = tid + u * NT;
+        if (e < NE) {
+            const int blk = e / (NB * NB), w = e % (NB * NB), ra = w % NB, cb = w / NB;
+            const int row = (blk == 0) ? ra : NB + ra;
+            const int col = (blk == 2) ? NB + cb : cb;
+            G[row + col * TWO] = acc[u];
+            if (blk == 1) G[col + row * TWO] = conj_s(acc[u]);
+        }
+    }
+}
+
+// ---- S3: the Hermitian eigensolver on each Gram block --------------------------
+// grid (count, L/2), GT threads.  J to global; flags the pair and the matrix.
+template <class T, int NB, int GT>
+__global__ void __launch_bounds__(GT) blk_heevj(const BlockedArgs a, int r) {
+    constexpr int TWO = 2 * NB, LDG = TWO + 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int b = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
+    int* pf = a.pairflag + (long long)b * (a.L / 2) + q;
+    if (blk_skip(a, b)) { if (tid == 0) *pf = 0; return; }
+    int bi, bj;
+    rr_pair(a.L, r, q, bi, bj);
+    if (bj >= a.l) { if (tid == 0) *pf = 0; return; }
+    T* G = reinterpret_cast<T*>(smem);
+    T* J = G + TWO * LDG;
+    const InnerTables<T, NB> tb(J + TWO * LDG);
+    const T* Gg = static_cast<const T*>(a.G) + b * a.sG + (long long)q * TWO * TWO;
+    for (int e = tid; e < TWO * TWO; e += GT) {       // upper triangle, mirrored
+        const int i = e % TWO, j = e / TWO;
+        if (i > j) continue;
+        T g = Gg[i + j * TWO];
+        if (i == j) g = make_s<T>(re(g));
+        G[i + j * LDG] = g;
+        G[j + i * LDG] = conj_s(g);
+    }
+    __syncthreads();
+    const int seen = inner_jacobi<T, NB, GT>(G, J, tb, (Real<T>)a.tol, a.inner_sweeps, tid, 1);
+    T* Jg = static_cast<T*>(a.J) + b * a.sJ + (long long)q * TWO * TWO;
+    for (int e = tid; e < TWO * TWO; e += GT) Jg[(e % TWO) + (e / TWO) * TWO] = J[(e % TWO) + (e / TWO) * LDG];
+    if (tid == 0) {
+        *pf = seen > 0;
+        if (seen > 0) a.state[4 * b + 1] = 1;
+    }
+}
+
+// panel row helpers: row `row` of [W; V] (rows 0..M-1 of W, then N of V)
+template <class T>
+__device__ __forceinline__ T* blk_row(const BlockedArgs& a, int b, int row, long long& ld) {
+    if (row < a.M) { ld = a.M; return static_cast<T*>(a.W) + b * a.sW + row; }
+    ld = a.N;
+    return static_cast<T*>(a.Vw) + b * a.sVw + (row - a.M);
+}
+
+// ---- S4/S5 fused (Design-3, Alg. 4): [P_i P_j] <- [P_i P_j] J, one read and one
+// write per element.  grid (count, L/2, row blocks), kUpdRows threads.
+template <class T, int NB>
+__global__ void __launch_bounds__(kUpdRows) blk_update_fused(const BlockedArgs a, int r) {
+    constexpr int TWO = 2 * NB;
+    extern __shared__ __align__(16) unsigned char smem_js[];
+    T* Js = reinterpret_cast<T*>(smem_js);
+    const int b = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
+    if (blk_skip(a, b)) return;
+    if (a.masks && !a.pairflag[(long long)b * (a.L / 2) + q]) return;
+    int bi, bj;
+    rr_pair(a.L, r, q, bi, bj);
+    if (bj >= a.l) return;
+    const T* Jg = static_cast<const T*>(a.J) + b * a.sJ + (long long)q * TWO * TWO;
+    for (int e = tid; e < TWO * TWO; e += kUpdRows) Js[e] = Jg[e];
+    __syncthreads();
+    const int row = blockIdx.z * kUpdRows + tid;
+    if (row >= a.M + a.N) return;
+    long long ld;
+    T* X = blk_row<T>(a, b, row, ld);
+    T x[TWO];
+#pragma unroll
+    for (int k = 0; k < TWO; ++k) x[k] = X[(long long)(k < NB ? bi * NB + k : bj * NB + k - NB) * ld];
+#pragma unroll
+    for (int c = 0; c < TWO; ++c) {
+        T acc = make_s<T>(0);
+#pragma unroll
+        for (int k = 0; k < TWO; ++k) acc = fma_s(x[k], Js[k + c * TWO], acc);
+        X[(long long)(c < NB ? bi * NB + c : bj * NB + c - NB) * ld] = acc;
+    }
+}
+
+// ---- S4/S5 baseline, stage 1 (Sec. 4.4): T_i = P_i J11, T_j = P_i J12 -------------
+template <class T, int NB>
+__global__ void __launch_bounds__(kUpdRows) blk_update_stage1(const BlockedArgs a, int r) {
+    constexpr int TWO = 2 * NB;
+    extern __shared__ __align__(16) unsigned char smem_js[];
+    T* Js = reinterpret_cast<T*>(smem_js);
+    const int b = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
+    if (blk_skip(a, b)) return;
+    if (a.masks && !a.pairflag[(long long)b * (a.L / 2) + q]) return;
+    int bi, bj;
+    rr_pair(a.L, r, q, bi, bj);
+    if (bj >= a.l) return;
+    const T* Jg = static_cast<const T*>(a.J) + b * a.sJ + (long long)q * TWO * TWO;
+    for (int e = tid; e < TWO * TWO; e += kUpdRows) Js[e] = Jg[e];
+    __syncthreads();
+    const int row = blockIdx.z * kUpdRows + tid, rows = a.M + a.N;
+    if (row >= rows) return;
+    long long ld;
+    const T* X = blk_row<T>(a, b, row, ld);
+    T* Tt = static_cast<T*>(a.T) + b * a.sT + (long long)q * rows * TWO + row;
+    T x[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) x[k] = X[(long long)(bi * NB + k) * ld];
+#pragma unroll
+    for (int c = 0; c < TWO; ++c) {
+        T acc = make_s<T>(0);
+#pragma unroll
+        for (int k = 0; k < NB; ++k) acc = fma_s(x[k], Js[k + c * TWO], acc);
+        Tt[(long long)c * rows] = acc;
+    }
+}
+
+// ---- stage 2: P_i = T_i + P_j J21, P_j = T_j + P_j J22 ------------------------------
+template <class T, int NB>
+__global__ void __launch_bounds__(kUpdRows) blk_update_stage2(const BlockedArgs a, int r) {
+    constexpr int TWO = 2 * NB;
+    extern __shared__ __align__(16) unsigned char smem_js[];
+    T* Js = reinterpret_cast<T*>(smem_js);
+    const int b = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
+    if (blk_skip(a, b)) return;
+    if (a.masks && !a.pairflag[(long long)b * (a.L / 2) + q]) return;
+    int bi, bj;
+    rr_pair(a.L, r, q, bi, bj);
+    if (bj >= a.l) return;
+    const T* Jg = static_cast<const T*>(a.J) + b * a.sJ + (long long)q * TWO * TWO;
+    for (int e = tid; e < TWO * TWO; e += kUpdRows) Js[e] = Jg[e];
+    __syncthreads();
+    const int row = blockIdx.z * kUpdRows + tid, rows = a.M + a.N;
+    if (row >= rows) return;
+    long long ld;
+    T* X = blk_row<T>(a, b, row, ld);
+    const T* Tt = static_cast<const T*>(a.T) + b * a.sT + (long long)q * rows * TWO + row;
+    T x[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) x[k] = X[(long long)(bj * NB + k) * ld];
+#pragma unroll
+    for (int c = 0; c < TWO; ++c) {
+        T acc = Tt[(long long)c * rows];
+#pragma unroll
+        for (int k = 0; k < NB; ++k) acc = fma_s(x[k], Js[NB + k + c * TWO], acc);
+        X[(long long)(c < NB ? bi * NB + c : bj * NB + c - NB) * ld] = acc;
+    }
+}
+
+// ---- a6: end of a sweep: count it, retire converged matrices ----------------------
+static __global__ void blk_converge(const BlockedArgs a) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= a.count) return;
+    int* s = a.state + 4 * b;
+    if (s[0] == 1) {
+        s[2] += 1;
+        if (!s[1]) s[0] = 0;               // a sweep without rotation: converged
+    }
+    s[1] = 0;
+    if (s[0] == 1) atomicOr(a.any_active, 1);
+}
+
+// ---- a7: finalise -------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(kBlkThreads) blk_finalize(const BlockedArgs a) {
+    using R = Real<T>;
+    constexpr int NT = kBlkThreads;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const int mid = blk_mid(a, b);
+    const int N = a.N, M = a.M;
+    R* red = reinterpret_cast<R*>(smem);                 // [NT/32]
+    int* iscr = reinterpret_cast<int*>(red + NT / 32);   // [4]
+    T* bcast = reinterpret_cast<T*>(iscr + 4);           // [2]
+    R* sig = reinterpret_cast<R*>(bcast + 2);            // [N]
+    int* rank = reinterpret_cast<int*>(sig + N);         // [N]
+    R* Sout = a.Sp ? static_cast<R*>(a.Sp[mid]) : static_cast<R*>(a.S) + (long long)mid * a.sS;
+    T* Uout = nullptr;
+    T* Vout = nullptr;
+    long long ldu = 1, ldv = 1;
+    if (a.wantU) {
+        Uout = a.Up ? static_cast<T*>(a.Up[mid]) : static_cast<T*>(a.U) + (long long)mid * a.sU;
+        ldu = a.ldup ? a.ldup[mid] : a.ldu;
+    }
+    if (a.wantV) {
+        Vout = a.Vp ? static_cast<T*>(a.Vp[mid]) : static_cast<T*>(a.V) + (long long)mid * a.sV;
+        ldv = a.ldvp ? a.ldvp[mid] : a.ldv;
+    }
+    const int status = a.state[4 * b], sw = a.state[4 * b + 2], ex = a.state[4 * b + 3];
+    if (status < 0) {
+        for (int e = tid; e < N; e += NT) Sout[e] = nan_s<R>();
+        if (Uout) for (int e = tid; e < a.m * N; e += NT) Uout[(e % a.m) + (long long)(e / a.m) * ldu] = nan_s<T>();
+        if (Vout) for (int e = tid; e < a.n * N; e += NT) Vout[(e % a.n) + (long long)(e / a.n) * ldv] = nan_s<T>();
+        if (tid == 0) {
+            a.info[mid] = -1;
+            if (a.sweeps) a.sweeps[mid] = 0;
+        }
+        return;
+    }
+    const T* W = static_cast<const T*>(a.W) + b * a.sW;
+    const T* V = static_cast<const T*>(a.Vw) + b * a.sVw;
+    T* scratch = static_cast<T*>(a.T) + b * a.sT;        // x (M), then E (N x N)
+    const bool needVs = a.trans ? a.wantU : a.wantV;
+    const bool wantWout = a.trans ? a.wantV : a.wantU;
+    T* Y = a.trans ? Vout : Uout;
+    T* Z = a.trans ? Uout : Vout;
+    const FinalScratch<T> fs{sig, rank, red, iscr, bcast};
+    finalize_outputs<T, NT>(W, M, V, N, M, N, ex, scratch, scratch + M, N,
+                            !(a.flags & 1), Sout, Y, a.trans ? ldv : ldu, wantWout, Z,
+                            a.trans ? ldu : ldv, needVs, fs);
+    if (tid == 0) {
+        a.info[mid] = status == 0 ? 0 : sw;
+        if (a.sweeps) a.sweeps[mid] = sw;
+    }
+}
+
+}  // namespace bsvd

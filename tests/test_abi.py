@@ -89,6 +89,16 @@ def test_workspace_query(L):
     assert n.value >= 4 * 3 * 4 and n.value % 256 == 0
     assert L.bsvd_gesvj_workspace(h, b"q", 3, m_arr, m_arr, 0, 1, 1, ctypes.byref(o), ctypes.byref(n)) == -1
     assert L.bsvd_last_arg(h) == 2
+    # shapes that do not fit on chip, and the paper's baseline path, need workspace
+    big = (ctypes.c_int * 1)(1000)
+    assert L.bsvd_gesvj_workspace(h, b"d", 2, big, big, 1, 1, 1, ctypes.byref(o), ctypes.byref(n)) == 0
+    assert n.value > 2 * 1000 * 1000 * 8
+    m64 = (ctypes.c_int * 1)(64)
+    plain = binding.make_opts(path="plain")
+    assert L.bsvd_gesvj_workspace(h, b"d", 4, m64, m64, 1, 1, 1, ctypes.byref(plain), ctypes.byref(n)) == 0
+    assert n.value > 4 * 3 * 64 * 64 * 8
+    fused = binding.make_opts(path="fused")
+    assert L.bsvd_gesvj_workspace(h, b"z", 1, big, big, 1, 1, 1, ctypes.byref(fused), ctypes.byref(n)) == -5
 
 
 def test_batched_invalid_arguments(L):
