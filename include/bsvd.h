@@ -135,6 +135,28 @@ bsvd_status bsvd_cgesvj_strided(BSVD_STRIDED_ARGS(void, float));    /* T = compl
 bsvd_status bsvd_zgesvj_strided(BSVD_STRIDED_ARGS(void, double));   /* T = complex double */
 
 /*
+ * Strided FP64 batch that allocates nothing (the paper has no counterpart).
+ * For callers that cannot allocate device memory: code inside a framework
+ * that owns the device-memory budget, code on a latency path where
+ * cudaMalloc's implicit device synchronisation is not acceptable, or callers
+ * with no allocator to size and pass a workspace.  Same arguments as
+ * bsvd_dgesvj_strided minus d_work / work_bytes; the multi-kernel path runs
+ * (PLAIN if opts->path asks for it, BLOCKED otherwise) with its workspace in a
+ * static 32 MiB device array that every GPU loading the library holds until
+ * exit.  A batch whose workspace exceeds 32 MiB (more than 203 matrices of
+ * 128 x 64) returns BSVD_ERR_WORKSPACE and launches nothing.  The first call
+ * on each device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the array, so calls that overlap on the GPU race: serialise them.
+ */
+bsvd_status bsvd_dgesvj_strided_noalloc(bsvd_handle handle, bsvd_job jobu, bsvd_job jobv, int batch,
+                                        int m, int n, const double* dA, int lda, long long strideA,
+                                        double* dS, long long strideS, double* dU, int ldu,
+                                        long long strideU, double* dV, int ldv, long long strideV,
+                                        int* d_info, int* d_sweeps, const bsvd_opts* opts,
+                                        void* stream);
+
+/*
  * Pointer-array batch (per-matrix shapes).  dA, dS, dU, dV are DEVICE arrays
  * of `batch` device pointers (as in batched BLAS); m, n, lda, ldu, ldv are
  * HOST arrays of `batch` ints.  Matrices are grouped by shape on the host and

@@ -33,6 +33,7 @@ EXPORTS = (
     "bsvd_version", "bsvd_gesvj_workspace",
     "bsvd_sgesvj_strided", "bsvd_dgesvj_strided", "bsvd_cgesvj_strided", "bsvd_zgesvj_strided",
     "bsvd_sgesvj_batched", "bsvd_dgesvj_batched", "bsvd_cgesvj_batched", "bsvd_zgesvj_batched",
+    "bsvd_dgesvj_strided_noalloc",
 )
 
 
