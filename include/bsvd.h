@@ -72,6 +72,14 @@ typedef enum {
                                fused update, masks); any matrix size; asynchronous      */
 } bsvd_path;
 
+typedef enum {
+    BSVD_PREC_NATIVE = 0,   /* every step in the working precision                          */
+    BSVD_PREC_MIXED = 1     /* FP64 output from mostly FP32 work: FP32 sweeps on an FP32 copy
+                               until the FP32 test passes, V restored to an orthonormal FP64
+                               matrix, A V formed in FP64, then FP64 polish sweeps until the
+                               FP64 test passes (d_sweeps reports the polish sweeps)         */
+} bsvd_prec;
+
 /* Solver options.  Zero-initialise, then set what you need; 0 = default. */
 typedef struct {
     int nb;            /* block width (Sec. 4); 0 = chosen from n and the type            */
@@ -85,7 +93,8 @@ typedef struct {
                           bit 2: no masks (Design-4 off; multi-kernel path, host-checked
                           batch convergence).  Bits 1-2 with AUTO select the multi-kernel
                           path.                                                              */
-    int reserved[6];
+    int prec;          /* bsvd_prec; MIXED only for d/z and the strided form                 */
+    int reserved[5];
 } bsvd_opts;
 
 /* Handle: caches device properties and per-device kernel set-up; owns no

@@ -48,7 +48,7 @@ class BsvdError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int), ("max_sweeps", ctypes.c_int), ("tol", ctypes.c_double),
                 ("inner_sweeps", ctypes.c_int), ("path", ctypes.c_int), ("flags", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("prec", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 _lock = threading.Lock()
@@ -106,10 +106,14 @@ def _check(st: int, where: str):
         raise BsvdError(st, where, L.bsvd_last_arg(h), L.bsvd_last_cuda(h))
 
 
-def make_opts(nb=0, tol=0.0, max_sweeps=0, inner_sweeps=0, path="auto", flags=0) -> Opts:
+PRECS = {"native": 0, "mixed": 1}
+
+
+def make_opts(nb=0, tol=0.0, max_sweeps=0, inner_sweeps=0, path="auto", flags=0, prec="native") -> Opts:
     o = Opts()
     o.nb, o.tol, o.max_sweeps, o.inner_sweeps = int(nb), float(tol), int(max_sweeps), int(inner_sweeps)
     o.path, o.flags = PATHS[path] if isinstance(path, str) else int(path), int(flags)
+    o.prec = PRECS[prec] if isinstance(prec, str) else int(prec)
     return o
 
 
@@ -156,7 +160,7 @@ def workspace_bytes(dtype, shapes, uniform: bool, compute_u=True, compute_v=True
 
 def gesvj(A: torch.Tensor, compute_u: bool = True, compute_v: bool = True, *, nb: int = 0,
           tol: float = 0.0, max_sweeps: int = 0, inner_sweeps: int = 0, path="auto",
-          flags: int = 0, out=None, work=None, stream=None) -> SVDResult:
+          flags: int = 0, prec="native", out=None, work=None, stream=None) -> SVDResult:
     """SVD of every matrix of a CUDA tensor A (batch, m, n) or (m, n).
 
     A may be float32, float64, complex64 or complex128; matrices are read
@@ -184,13 +188,13 @@ def gesvj(A: torch.Tensor, compute_u: bool = True, compute_v: bool = True, *, nb
         sweeps = torch.empty(batch, dtype=torch.int32, device=dev)
     else:
         S, U, V, info, sweeps = out
-    o = make_opts(nb, tol, max_sweeps, inner_sweeps, path, flags)
+    o = make_opts(nb, tol, max_sweeps, inner_sweeps, path, flags, prec)
     t = DTYPES[A.dtype]
     L = load()
     if work is None:
         nbytes = workspace_bytes(A.dtype, [(m, n)], True, compute_u, compute_v, batch=batch, nb=nb,
                                  tol=tol, max_sweeps=max_sweeps, inner_sweeps=inner_sweeps,
-                                 path=path, flags=flags)
+                                 path=path, flags=flags, prec=prec)
         work = torch.empty(nbytes, dtype=torch.uint8, device=dev) if nbytes else None
     f = getattr(L, f"bsvd_{t}gesvj_strided")
     st = f(handle(), int(compute_u), int(compute_v), batch, m, n,

@@ -23,6 +23,7 @@ struct BlockedArgs {
     int* any_active;           // one int: some matrix still active after a sweep
     // caller's arrays (as FusedArgs)
     const void* A; long long sA; int lda; const void* const* Ap; const int* ldap;
+    const void* V0; long long sV0; int ldv0;   // initial V (N x N, by matrix id) or nullptr for I
     void* S; long long sS; void* const* Sp;
     void* U; long long sU; int ldu; void* const* Up; const int* ldup;
     void* V; long long sV; int ldv; void* const* Vp; const int* ldvp;

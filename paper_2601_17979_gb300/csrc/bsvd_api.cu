@@ -61,7 +61,7 @@ bsvd_status refresh_device(bsvd_handle h) {
 }
 
 struct Resolved {
-    int nb, max_sweeps, inner_sweeps, path, flags;
+    int nb, max_sweeps, inner_sweeps, path, flags, prec;
     double tol;
 };
 
@@ -71,7 +71,8 @@ bool resolve(const bsvd_opts* o, bool single, int N, Resolved& r) {
     std::memset(&z, 0, sizeof z);
     if (!o) o = &z;
     if (o->nb < 0 || o->max_sweeps < 0 || o->inner_sweeps < 0 || o->tol < 0 || o->path < 0 ||
-        o->path > BSVD_PATH_BLOCKED || o->flags < 0 || o->flags > 7)
+        o->path > BSVD_PATH_BLOCKED || o->flags < 0 || o->flags > 7 || o->prec < 0 ||
+        o->prec > BSVD_PREC_MIXED || (o->prec == BSVD_PREC_MIXED && single))
         return false;
     r.nb = o->nb ? o->nb : (N >= 48 ? 16 : (N >= 12 ? 8 : 4));
     r.max_sweeps = o->max_sweeps ? o->max_sweeps : kDefaultMaxSweeps;
@@ -80,6 +81,7 @@ bool resolve(const bsvd_opts* o, bool single, int N, Resolved& r) {
     r.inner_sweeps = o->inner_sweeps ? o->inner_sweeps : (r.path == BSVD_PATH_PLAIN ? 30 : 1);
     r.tol = o->tol > 0 ? o->tol : 30.0 * (single ? kU32 : kU64);
     r.flags = o->flags;
+    r.prec = o->prec;
     return true;
 }
 
@@ -177,6 +179,120 @@ int device_smem_or_default(bsvd_handle h) {
     return 232448;   // GB300: 227 KB opt-in shared memory per block
 }
 
+// ---- mixed precision (FP64 output from FP32 sweeps + FP64 polish) ----------
+struct MixedPlan {
+    Plan p32, p64;
+    Resolved r32, r64;
+    size_t off[8];        // A32, V32, S32, info32, V64, Vtmp, E, Ahat
+    size_t off32, off64;  // workspace of the two solves (multi-kernel paths)
+    size_t bytes;
+};
+
+bsvd_status plan_mixed(int max_smem, char t, int m, int n, int batch, bool wantU, bool wantV,
+                       const Resolved& r, MixedPlan& mp) {
+    const int M = std::max(m, n), N = std::min(m, n);
+    const TypeOps o32 = ops_for(t == 'd' ? 's' : 'c'), o64 = ops_for(t);
+    const bool trans = m < n;
+    mp.r32 = r;
+    mp.r32.tol = 30.0 * kU32;
+    mp.r32.path = BSVD_PATH_AUTO;
+    mp.r32.flags = 0;
+    mp.r32.inner_sweeps = 1;
+    mp.r32.prec = BSVD_PREC_NATIVE;
+    mp.r64 = r;
+    mp.r64.prec = BSVD_PREC_NATIVE;
+    // FP32 solve: V only, on the working-orientation copy (M x N)
+    bsvd_status st = plan_group(max_smem, o32, M, N, batch, false, true, mp.r32, mp.p32);
+    if (st != BSVD_OK) return st;
+    // FP64 polish on A_hat (M x N); its U/V are the caller's U/V, swapped for m < n
+    const bool pu = trans ? wantV : wantU, pv = trans ? wantU : wantV;
+    st = plan_group(max_smem, o64, M, N, batch, pu, pv, mp.r64, mp.p64);
+    if (st != BSVD_OK) return st;
+    const size_t b = (size_t)batch, mn = (size_t)M * N, nn = (size_t)N * N;
+    const size_t sizes[8] = {b * mn * o32.elt, b * nn * o32.elt, b * N * 4, b * 2 * sizeof(int),
+                             b * nn * o64.elt, b * nn * o64.elt, b * nn * o64.elt, b * mn * o64.elt};
+    size_t pos = 0;
+    for (int i = 0; i < 8; ++i) { mp.off[i] = pos; pos += align256(sizes[i]); }
+    mp.off32 = pos;
+    if (mp.p32.blocked) pos += align256(mp.p32.bytes);
+    mp.off64 = pos;
+    if (mp.p64.blocked) pos += align256(mp.p64.bytes);
+    mp.bytes = pos;
+    return BSVD_OK;
+}
+
+bsvd_status mixed_impl(char t, bsvd_handle h, bool wantU, bool wantV, int batch, int m, int n,
+                       const void* dA, int lda, long long sA, void* dS, long long sS, void* dU,
+                       int ldu, long long sU, void* dV, int ldv, long long sV, int* d_info,
+                       int* d_sweeps, void* d_work, size_t work_bytes, const Resolved& r,
+                       cudaStream_t s) {
+    MixedPlan mp;
+    bsvd_status st = plan_mixed(h->max_smem, t, m, n, batch, wantU, wantV, r, mp);
+    if (st != BSVD_OK) return st;
+    if (!d_work || work_bytes < mp.bytes) return BSVD_ERR_WORKSPACE;
+    const int M = std::max(m, n), N = std::min(m, n);
+    const bool trans = m < n;
+    char* w = static_cast<char*>(d_work);
+    bsvd::MixedArgs ma;
+    ma.m = m; ma.n = n; ma.M = M; ma.N = N; ma.trans = trans;
+    ma.A = dA; ma.sA = sA; ma.lda = lda;
+    ma.A32 = w + mp.off[0]; ma.V32 = w + mp.off[1];
+    ma.V64 = w + mp.off[4]; ma.Vtmp = w + mp.off[5]; ma.E = w + mp.off[6]; ma.Ahat = w + mp.off[7];
+    void* S32 = w + mp.off[2];
+    int* info32 = reinterpret_cast<int*>(w + mp.off[3]);
+    int* sweeps32 = info32 + batch;
+    const TypeOps o32 = ops_for(t == 'd' ? 's' : 'c'), o64 = ops_for(t);
+    cudaError_t e = (t == 'd') ? bsvd::mixed_prepare_d(ma, batch, s) : bsvd::mixed_prepare_z(ma, batch, s);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    // 1. FP32 solve for V32 (N x N, ld N)
+    if (mp.p32.blocked) {
+        BlockedArgs a = blocked_args(M, N, batch, false, true, mp.r32, mp.p32.masks);
+        a.A = ma.A32; a.sA = (long long)M * N; a.lda = M;
+        a.S = S32; a.sS = N;
+        a.V = ma.V32; a.sV = (long long)N * N; a.ldv = N;
+        a.info = info32; a.sweeps = sweeps32;
+        e = o32.blocked(mp.p32.nb, a, w + mp.off32, s, mp.p32.two_stage, mp.p32.host_sync);
+    } else {
+        FusedArgs& a = mp.p32.a;
+        a.A = ma.A32; a.sA = (long long)M * N; a.lda = M;
+        a.S = S32; a.sS = N;
+        a.V = ma.V32; a.sV = (long long)N * N; a.ldv = N;
+        a.info = info32; a.sweeps = sweeps32;
+        e = o32.launch(mp.p32.nb, a, batch, mp.p32.smem, s);
+    }
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    // 2. orthonormal V in FP64 and A_hat = A V
+    e = (t == 'd') ? bsvd::mixed_restore_d(ma, batch, s) : bsvd::mixed_restore_z(ma, batch, s);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    // 3. FP64 polish on A_hat from V64; outputs go straight to the caller (U and V
+    //    swap roles for m < n: A^H = V Sigma U^H)
+    void* pU = trans ? dV : dU;
+    void* pV = trans ? dU : dV;
+    const int pldu = trans ? ldv : ldu, pldv = trans ? ldu : ldv;
+    const long long psU = trans ? sV : sU, psV = trans ? sU : sV;
+    const bool pu = trans ? wantV : wantU, pv = trans ? wantU : wantV;
+    if (mp.p64.blocked) {
+        BlockedArgs a = blocked_args(M, N, batch, pu, pv, mp.r64, mp.p64.masks);
+        a.A = ma.Ahat; a.sA = (long long)M * N; a.lda = M;
+        a.V0 = pv ? ma.V64 : nullptr; a.sV0 = (long long)N * N; a.ldv0 = N;
+        a.S = dS; a.sS = sS;
+        a.U = pU; a.sU = psU; a.ldu = pldu;
+        a.V = pV; a.sV = psV; a.ldv = pldv;
+        a.info = d_info; a.sweeps = d_sweeps;
+        e = o64.blocked(mp.p64.nb, a, w + mp.off64, s, mp.p64.two_stage, mp.p64.host_sync);
+    } else {
+        FusedArgs& a = mp.p64.a;
+        a.A = ma.Ahat; a.sA = (long long)M * N; a.lda = M;
+        a.V0 = pv ? ma.V64 : nullptr; a.sV0 = (long long)N * N; a.ldv0 = N;
+        a.S = dS; a.sS = sS;
+        a.U = pU; a.sU = psU; a.ldu = pldu;
+        a.V = pV; a.sV = psV; a.ldv = pldv;
+        a.info = d_info; a.sweeps = d_sweeps;
+        e = o64.launch(mp.p64.nb, a, batch, mp.p64.smem, s);
+    }
+    return e == cudaSuccess ? BSVD_OK : fail_cuda(h, e);
+}
+
 bsvd_status strided_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, int batch, int m,
                          int n, const void* dA, int lda, long long sA, void* dS, long long sS,
                          void* dU, int ldu, long long sU, void* dV, int ldv, long long sV,
@@ -216,6 +332,9 @@ bsvd_status strided_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
         if (e == cudaSuccess && d_sweeps) e = cudaMemsetAsync(d_sweeps, 0, sizeof(int) * (size_t)batch, s);
         return e == cudaSuccess ? BSVD_OK : fail_cuda(h, e);
     }
+    if (r.prec == BSVD_PREC_MIXED)
+        return mixed_impl(t, h, wantU, wantV, batch, m, n, dA, lda, sA, dS, sS, dU, ldu, sU, dV,
+                          ldv, sV, d_info, d_sweeps, d_work, work_bytes, r, s);
     Plan p;
     st = plan_group(h->max_smem, ops, m, n, batch, wantU, wantV, r, p);
     if (st != BSVD_OK) return st;
@@ -295,6 +414,7 @@ bsvd_status batched_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
     }
     if (d_work && (reinterpret_cast<uintptr_t>(d_work) & 15) != 0) return fail_arg(h, 16);
     const TypeOps ops = ops_for(t);
+    if (opts && opts->prec == BSVD_PREC_MIXED) return BSVD_ERR_NOT_IMPLEMENTED;   // strided form only
     Groups groups;
     for (int i = 0; i < batch; ++i) groups[{m[i], n[i]}].push_back(i);
     // plan every group before touching the device, so a bad shape fails cleanly
@@ -427,6 +547,12 @@ bsvd_status bsvd_gesvj_workspace(bsvd_handle handle, char dtype, int batch, cons
         if (std::min(m, n) == 0) return BSVD_OK;
         Resolved r;
         if (!resolve(opts, ops.single, std::min(m, n), r)) return fail_arg(handle, 9);
+        if (r.prec == BSVD_PREC_MIXED) {
+            MixedPlan mp;
+            bsvd_status st = plan_mixed(max_smem, dtype, m, n, batch, wantU, wantV, r, mp);
+            if (st == BSVD_OK) *bytes = mp.bytes;
+            return st;
+        }
         Plan p;
         bsvd_status st = plan_group(max_smem, ops, m, n, batch, wantU, wantV, r, p);
         if (st != BSVD_OK) return st;
@@ -439,6 +565,7 @@ bsvd_status bsvd_gesvj_workspace(bsvd_handle handle, char dtype, int batch, cons
         if (n_arr[i] < 0) return fail_arg(handle, 5);
         groups[{m_arr[i], n_arr[i]}].push_back(i);
     }
+    if (opts && opts->prec == BSVD_PREC_MIXED) return BSVD_ERR_NOT_IMPLEMENTED;   // strided form only
     std::vector<Plan> plans;
     std::vector<Resolved> res;
     bsvd_status st = plan_batched(max_smem, ops, batch, groups, wantU, wantV, opts, plans, res, *bytes);

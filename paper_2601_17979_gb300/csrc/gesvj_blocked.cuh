@@ -75,7 +75,11 @@ __global__ void __launch_bounds__(kBlkThreads) blk_load(const BlockedArgs a) {
         else         W[i + (long long)j * M] = x;
     }
     for (int e = tid; e < M * (a.Np - N); e += NT) W[(e % M) + (long long)(N + e / M) * M] = make_s<T>(0);
-    for (int e = tid; e < N * a.Np; e += NT) V[(e % N) + (long long)(e / N) * N] = make_s<T>((e % N) == (e / N) ? 1 : 0);
+    const T* V0 = a.V0 ? static_cast<const T*>(a.V0) + (long long)mid * a.sV0 : nullptr;
+    for (int e = tid; e < N * a.Np; e += NT) {
+        const int i = e % N, j = e / N;
+        V[i + (long long)j * N] = (V0 && j < N) ? V0[i + (long long)j * a.ldv0] : make_s<T>(i == j && !V0 ? 1 : 0);
+    }
 }
 
 // ---- S2: G = [A_i A_j]^H [A_i A_j] as three nb x nb products -----------------
@@ -96,9 +100,12 @@ __global__ void __launch_bounds__(kBlkThreads) blk_gram(const BlockedArgs a, int
     if (bj >= a.l) return;
     const T* W = static_cast<const T*>(a.W) + b * a.sW;
     const int M = a.M;
-    T acc[PER];
+    // two partial sums per entry, rows [0, M/2) and [M/2, M), added at the end
+    // (the same summation as the on-chip kernel)
+    T lo[PER], hi[PER];
 #pragma unroll
-    for (int u = 0; u < PER; ++u) acc[u] = make_s<T>(0);
+    for (int u = 0; u < PER; ++u) { lo[u] = make_s<T>(0); hi[u] = make_s<T>(0); }
+    const int mh = M / 2;
     for (int k0 = 0; k0 < M; k0 += KC) {
         const int kc = min(KC, M - k0);
         for (int e = tid; e < KC * TWO; e += NT) {
@@ -114,13 +121,19 @@ __global__ void __launch_bounds__(kBlkThreads) blk_gram(const BlockedArgs a, int
                 const int blk = e / (NB * NB), w = e % (NB * NB), ra = w % NB, cb = w / NB;
                 const int row = (blk == 0) ? ra : NB + ra;      // (i,i), (j,i), (j,j)
                 const int col = (blk == 2) ? NB + cb : cb;
-                T s = acc[u];
-                for (int kk = 0; kk < kc; ++kk) s = cfma(P[kk + row * KC], P[kk + col * KC], s);
-                acc[u] = s;
+                const int split = min(max(mh - k0, 0), kc);    // rows of this chunk below M/2
+                T s0 = lo[u], s1 = hi[u];
+                for (int kk = 0; kk < split; ++kk) s0 = cfma(P[kk + row * KC], P[kk + col * KC], s0);
+                for (int kk = split; kk < kc; ++kk) s1 = cfma(P[kk + row * KC], P[kk + col * KC], s1);
+                lo[u] = s0;
+                hi[u] = s1;
             }
         }
         __syncthreads();
     }
+    T acc[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) acc[u] = add(lo[u], hi[u]);
     T* G = static_cast<T*>(a.G) + b * a.sG + (long long)q * TWO * TWO;
 #pragma unroll
     for (int u = 0; u < PER; ++u) {

@@ -34,6 +34,7 @@ struct FusedArgs {
     int offW, offV, offG, offMisc, groupBytes;
     // strided addressing (p* == nullptr) or pointer arrays
     const void* A; long long sA; int lda; const void* const* Ap; const int* ldap;
+    const void* V0; long long sV0; int ldv0;   // initial V (N x N, by matrix id) or nullptr for I
     void* S; long long sS; void* const* Sp;
     void* U; long long sU; int ldu; void* const* Up; const int* ldup;
     void* V; long long sV; int ldv; void* const* Vp; const int* ldvp;
@@ -92,8 +93,13 @@ gesvj_fused_kernel(const FusedArgs a) {
         else         W[i + j * ldw] = x;
     }
     for (int e = tid; e < M * (a.Np - N); e += NT) W[(e % M) + (N + e / M) * ldw] = make_s<T>(0);
-    if (needVs)
-        for (int e = tid; e < N * a.Np; e += NT) Vs[(e % N) + (e / N) * ldvs] = make_s<T>((e % N) == (e / N) ? 1 : 0);
+    if (needVs) {
+        const T* V0 = a.V0 ? static_cast<const T*>(a.V0) + (long long)mid * a.sV0 : nullptr;
+        for (int e = tid; e < N * a.Np; e += NT) {
+            const int i = e % N, j = e / N;
+            Vs[i + j * ldvs] = (V0 && j < N) ? V0[i + (long long)j * a.ldv0] : make_s<T>(i == j && !V0 ? 1 : 0);
+        }
+    }
     mx = warp_max(mx);
     const bool wbad = __any_sync(0xffffffffu, nonfin);
     if (lane == 0) red[warp] = wbad ? R(-1) : mx;             // -1 marks a non-finite entry
@@ -154,18 +160,30 @@ gesvj_fused_kernel(const FusedArgs a) {
                 if (bj >= a.l) continue;                       // phantom block
                 auto col = [&](int c) { return c < NB ? bi * NB + c : bj * NB + (c - NB); };
 
-                // S2: G = P^H P, upper triangle, mirrored to keep G Hermitian
-                constexpr int NUP = TWO * (TWO + 1) / 2;
-                for (int e = gt; e < NUP; e += GT) {
-                    int ca, cb;
-                    tri_index(e, ca, cb);
-                    const T* x = W + col(ca) * ldw;
-                    const T* y = W + col(cb) * ldw;
-                    T acc = make_s<T>(0);
-                    for (int k = 0; k < M; ++k) acc = cfma(x[k], y[k], acc);
-                    if (ca == cb) acc = make_s<T>(re(acc));
-                    G[ca + cb * LDG] = acc;
-                    G[cb + ca * LDG] = conj_s(acc);
+                // S2: G = P^H P, upper triangle, mirrored to keep G Hermitian.
+                // Lanes l and l+16 of a warp sum the same entry over the two
+                // halves of the rows [0, M/2) and [M/2, M); one shuffle adds them.
+                {
+                    constexpr int NUP = TWO * (TWO + 1) / 2, NWG = GT / 32;
+                    const int wg = gt >> 5, kh = (gt >> 4) & 1, el = gt & 15;
+                    const int kb = kh ? M / 2 : 0, ke = kh ? M : M / 2;
+                    for (int e0 = wg * 16; e0 < NUP; e0 += NWG * 16) {
+                        const int e = e0 + el;
+                        int ca = 0, cb = 0;
+                        T acc = make_s<T>(0);
+                        if (e < NUP) {
+                            tri_index(e, ca, cb);
+                            const T* x = W + col(ca) * ldw;
+                            const T* y = W + col(cb) * ldw;
+                            for (int k = kb; k < ke; ++k) acc = cfma(x[k], y[k], acc);
+                        }
+                        acc = add(acc, shfl_xor_s(acc, 16));
+                        if (kh == 0 && e < NUP) {
+                            if (ca == cb) acc = make_s<T>(re(acc));
+                            G[ca + cb * LDG] = acc;
+                            G[cb + ca * LDG] = conj_s(acc);
+                        }
+                    }
                 }
                 group_sync(g, GT);
 
@@ -174,22 +192,36 @@ gesvj_fused_kernel(const FusedArgs a) {
                 if (seen == 0) continue;                       // J = I: pair masked (Design-4)
                 if (gt == 0) swflag[sw] = 1;
 
-                // S4/S5: [W_i W_j] <- [W_i W_j] J and [V_i V_j] <- [V_i V_j] J
-                const int rows = M + (needVs ? N : 0);
-                for (int i = gt; i < rows; i += GT) {
-                    T* X;
-                    int ld, row;
-                    if (i < M) { X = W; ld = ldw; row = i; }
-                    else       { X = Vs; ld = ldvs; row = i - M; }
-                    T x[TWO];
+                // S4/S5: [W_i W_j] <- [W_i W_j] J and [V_i V_j] <- [V_i V_j] J.
+                // A warp takes 16 rows at a time; lanes l and l+16 both read row
+                // l and write the first and the second nb outputs of it, so the
+                // M + n rows spread evenly over the group.
+                {
+                    const int rows = M + (needVs ? N : 0);
+                    const int wg = gt >> 5, half = (gt >> 4) & 1, rl = gt & 15;
+                    constexpr int NWG = GT / 32;
+                    for (int r0 = wg * 16; r0 < rows; r0 += NWG * 16) {
+                        const int i = r0 + rl;
+                        const bool ok = i < rows;
+                        T* X = W;
+                        int ld = ldw, row = i;
+                        if (i >= M) { X = Vs; ld = ldvs; row = i - M; }
+                        T x[TWO];
+                        if (ok) {
 #pragma unroll
-                    for (int k = 0; k < TWO; ++k) x[k] = X[row + col(k) * ld];
+                            for (int k = 0; k < TWO; ++k) x[k] = X[row + col(k) * ld];
+                        }
+                        __syncwarp();
+                        if (ok) {
 #pragma unroll
-                    for (int c = 0; c < TWO; ++c) {
-                        T acc = make_s<T>(0);
+                            for (int c = 0; c < NB; ++c) {
+                                const int cc = half * NB + c;
+                                T acc = make_s<T>(0);
 #pragma unroll
-                        for (int k = 0; k < TWO; ++k) acc = fma_s(x[k], J[k + c * LDG], acc);
-                        X[row + col(c) * ld] = acc;
+                                for (int k = 0; k < TWO; ++k) acc = fma_s(x[k], J[k + cc * LDG], acc);
+                                X[row + col(cc) * ld] = acc;
+                            }
+                        }
                     }
                 }
                 group_sync(g, GT);

@@ -10,6 +10,22 @@ namespace bsvd {
 struct FusedArgs;
 struct BlockedArgs;
 
+// Buffers of the mixed-precision path (strided batches; per matrix, in the
+// working orientation M = max(m, n) rows, N = min(m, n) columns).
+struct MixedArgs {
+    int m, n, M, N, trans;
+    const void* A; long long sA; int lda;   // the caller's FP64 / complex128 A
+    void* A32;                              // M x N, ld M: FP32 copy of 2^-ex A (or A^H)
+    void* V32;                              // N x N, ld N: V of the FP32 solve
+    void* V64; void* Vtmp; void* E;         // N x N, ld N, FP64: restored V and scratch
+    void* Ahat;                             // M x N, ld M, FP64: A V
+};
+
+cudaError_t mixed_prepare_d(const MixedArgs& a, int batch, cudaStream_t st);
+cudaError_t mixed_prepare_z(const MixedArgs& a, int batch, cudaStream_t st);
+cudaError_t mixed_restore_d(const MixedArgs& a, int batch, cudaStream_t st);
+cudaError_t mixed_restore_z(const MixedArgs& a, int batch, cudaStream_t st);
+
 // Bytes of workspace the multi-kernel path needs for `count` matrices of one
 // shape (defined in bsvd_api.cu from the same layout as blocked_launch.cuh).
 size_t blocked_bytes(int nb, int M, int N, int count, bool two_stage, size_t elt);

@@ -49,6 +49,14 @@ template <class R> __device__ __forceinline__ R warp_sum(R v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+__device__ __forceinline__ float shfl_xor_s(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_xor_s(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ float2 shfl_xor_s(float2 v, int o) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+__device__ __forceinline__ double2 shfl_xor_s(double2 v, int o) {
+    return make_double2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
 __device__ __forceinline__ float warp_sum_s(float v) { return warp_sum(v); }
 __device__ __forceinline__ double warp_sum_s(double v) { return warp_sum(v); }
 __device__ __forceinline__ float2 warp_sum_s(float2 v) { return make_float2(warp_sum(v.x), warp_sum(v.y)); }
@@ -109,11 +117,13 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
                 R c = 1, sn = 0, t = 0;
                 T ph = make_s<T>(1);
                 if (fire) {
-                    const R tau = (gpp - gqq) / (2 * apq);
-                    t = (tau >= 0 ? R(1) : R(-1)) / (fabs(tau) + hypot_r(R(1), tau));
-                    c = R(1) / sqrt_r(R(1) + t * t);
+                    // Eq. (sin-cos) with tau = x / y, x = g_pp - g_qq, y = 2 |g_pq|:
+                    // t = sign(tau) / (|tau| + sqrt(1 + tau^2)) = sign(x) y / (|x| + hypot(x, y))
+                    const R x = gpp - gqq, y = 2 * apq;
+                    t = (x >= 0 ? y : -y) / (fabs(x) + hypot_r(x, y));
+                    c = rsqrt_r(R(1) + t * t);
                     sn = t * c;
-                    ph = divr(gpq, apq);
+                    ph = phase_s(gpq, apq);
                     atomicAdd(tb.count, 1);
                 }
                 tb.c[gt] = c; tb.s[gt] = sn; tb.t[gt] = t; tb.ph[gt] = ph;

@@ -122,6 +122,17 @@ template <> __device__ __forceinline__ double nan_s<double>() { return __longlon
 template <> __device__ __forceinline__ float2 nan_s<float2>() { return make_float2(nan_s<float>(), nan_s<float>()); }
 template <> __device__ __forceinline__ double2 nan_s<double2>() { return make_double2(nan_s<double>(), nan_s<double>()); }
 
+// 1/sqrt(x): rsqrtf (within 2 ulp) for float, the double-precision rsqrt
+// (within 1 ulp) for double -- a rotation only needs c^2 + s^2 = 1 to a few ulp.
+__device__ __forceinline__ float rsqrt_r(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_r(double x) { return rsqrt(x); }
+
+// e^{i arg(g)} given a = |g| > 0: the sign for real data
+__device__ __forceinline__ float phase_s(float g, float) { return copysignf(1.0f, g); }
+__device__ __forceinline__ double phase_s(double g, double) { return copysign(1.0, g); }
+__device__ __forceinline__ float2 phase_s(float2 g, float a) { const float r = 1.0f / a; return make_float2(g.x * r, g.y * r); }
+__device__ __forceinline__ double2 phase_s(double2 g, double a) { const double r = 1.0 / a; return make_double2(g.x * r, g.y * r); }
+
 __device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
 __device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
 __device__ __forceinline__ float hypot_r(float a, float b) { return hypotf(a, b); }

@@ -66,6 +66,9 @@ def test_strided_invalid_argument_positions(L, field, value, pos):
 def test_invalid_options(L):
     assert call_strided(L, opts=dict(nb=-1)) == -1
     assert L.bsvd_last_arg(bsvd.handle()) == 22
+    # mixed precision exists for FP64 output only
+    assert call_strided(L, t="s", opts=dict(prec="mixed")) == -1
+    assert L.bsvd_last_arg(bsvd.handle()) == 22
 
 
 def test_empty_batch_is_a_noop(L):
@@ -97,6 +100,9 @@ def test_workspace_query(L):
     plain = binding.make_opts(path="plain")
     assert L.bsvd_gesvj_workspace(h, b"d", 4, m64, m64, 1, 1, 1, ctypes.byref(plain), ctypes.byref(n)) == 0
     assert n.value > 4 * 3 * 64 * 64 * 8
+    mixed = binding.make_opts(prec="mixed")
+    assert L.bsvd_gesvj_workspace(h, b"d", 4, m64, m64, 1, 1, 1, ctypes.byref(mixed), ctypes.byref(n)) == 0
+    assert n.value > 4 * (64 * 64 * (4 + 4 + 8 * 4))
     fused = binding.make_opts(path="fused")
     assert L.bsvd_gesvj_workspace(h, b"z", 1, big, big, 1, 1, 1, ctypes.byref(fused), ctypes.byref(n)) == -5
 
