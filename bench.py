@@ -193,6 +193,109 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_uneven(args, rank, world, local):
+    """Uneven sizes: one persistent launch per type vs one launch per shape."""
+    import torch
+    import paper_2601_17979_gb300 as bsvd
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    bsvd.build()
+    B = args.batch if args.batch != BATCH else 20000
+    ids = range(rank * B, (rank + 1) * B)
+    mats = synth.matrices("uneven", ids)
+    groups = {}
+    for x in mats:
+        groups.setdefault(x.dtype, []).append(x)
+    dev_mats = {dt: [torch.from_numpy(x).to(dev) for x in lst] for dt, lst in groups.items()}
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def solve_all(path):
+        res = {}
+        for dt, T in dev_mats.items():
+            res[dt] = bsvd.gesvj_batched(T, path=path)
+        return res
+
+    for _ in range(max(1, args.warmup)):
+        solve_all("persistent")
+    barrier()
+    sampler = ClockSampler(gpu_uuid(torch, dev))
+    with sampler:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            res = solve_all("persistent")
+        b.record(stream)
+        barrier()
+    ms = a.elapsed_time(b) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = B * world / (ms * 1e-3)
+    flops = 0.0
+    for dt, r in res.items():
+        sw = r.sweeps.cpu().numpy()
+        for x, k in zip(groups[dt], sw):
+            m, n = x.shape
+            f = matrix_flops(max(m, n), min(m, n), 16, [k])
+            flops += 4 * f if np.iscomplexobj(x) else f
+    info = np.concatenate([r.info.cpu().numpy() for r in res.values()])
+    line = {"metric": "batch SVD matrices/s (uneven sizes, FP32 + complex64)", "value": value,
+            "unit": "matrices/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+c64", "data": "synthetic",
+            "config": {"workload": "uneven: m ~ U{8..512}, n ~ U{8..m}, entries U(-1,1), half complex64",
+                       "matrices_per_rank": B, "path": "one persistent launch per type",
+                       "l2": "inputs larger than L2"},
+            "gpu_launches": 2 * args.steps, "info_nonzero": int((info != 0).sum()),
+            "gflops": flops / (ms * 1e-3) / 1e9,
+            "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAK_FP32 / 1e12,
+                         "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAK_FP32, "traffic": None},
+            "clocks": sampler.summary()}
+    # the same matrices with one launch per distinct shape (the pointer-array
+    # form grouping by shape) -- the path the persistent launch replaces
+    # (timed on the first 500 matrices: nearly every shape is distinct, so it
+    # runs one launch -- or one multi-kernel sweep loop -- per matrix)
+    sub = {}
+    for x in mats[:min(B, 500)]:
+        sub.setdefault(x.dtype, []).append(torch.from_numpy(x).to(dev))
+    barrier()
+    a.record(stream)
+    for dt, T in sub.items():
+        bsvd.gesvj_batched(T, path="auto")
+    b.record(stream)
+    barrier()
+    per_shape = a.elapsed_time(b)
+    nsub = sum(len(T) for T in sub.values())
+    line["one_launch_per_shape"] = {"matrices_per_s": nsub / (per_shape * 1e-3), "ms": per_shape,
+                                    "matrices": nsub,
+                                    "distinct_shapes": len({x.shape + (x.dtype,) for x in mats[:nsub]}),
+                                    "persistent_speedup": (per_shape / nsub) / (ms / B)}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        S = min(args.cpu_sample, 400)
+        sample = mats[:S]
+        t0 = time.perf_counter()
+        r = oracle.default().gesvj(sample)
+        dt_ = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": S / dt_, "unit": "matrices/s", "cores": r["threads"], "kind": "oracle",
+                                "sample": f"first {S} matrices of the same workload, Alg. 2 in FP64, "
+                                          f"OpenMP over matrices ({dt_:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def config_dict(world, per_rank):
     return {"workload": "tall128x64: 10,000 FP64 (sigma geometric 1..1e-6) + 10,000 FP32 "
                         "(1..1e-3) matrices 128x64 = Q1 diag(sigma) Q2^T, Haar Q1, Q2",
@@ -214,6 +317,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 baseline path")
     ap.add_argument("--ladder", action="store_true", help="also time Design-2/3/4 (multi-kernel)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision FP64 leg")
+    ap.add_argument("--workload", default="tall128x64", choices=["tall128x64", "uneven"],
+                    help="tall128x64 (default) or uneven: 10,000 FP32 + 10,000 complex64 matrices, "
+                         "m ~ U{8..512}, n ~ U{8..m}, one persistent launch per type")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
 
@@ -223,6 +329,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "uneven":
+        run_uneven(args, rank, world, local)
         return
 
     import torch

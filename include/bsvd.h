@@ -68,8 +68,12 @@ typedef enum {
                                inner sweeps), two-stage vector update, no masks, batch-
                                level convergence checked on the host once per sweep (the
                                call then synchronises `stream`); FP64 comparison path   */
-    BSVD_PATH_BLOCKED = 3   /* the multi-kernel path with Designs 2-4 (one inner sweep,
+    BSVD_PATH_BLOCKED = 3,  /* the multi-kernel path with Designs 2-4 (one inner sweep,
                                fused update, masks); any matrix size; asynchronous      */
+    BSVD_PATH_PERSISTENT = 4 /* pointer-array form: all shapes in one persistent launch;
+                               CTAs take matrices from a work queue, largest first, each
+                               solved whole with W and V in a per-CTA workspace slot
+                               (the strided form treats it as AUTO)                      */
 } bsvd_path;
 
 typedef enum {

@@ -20,7 +20,7 @@ from . import buildlib as _build
 BSVD_OK = 0
 STATUS = {0: "BSVD_OK", -1: "BSVD_ERR_INVALID", -2: "BSVD_ERR_WORKSPACE", -3: "BSVD_ERR_CUDA",
           -4: "BSVD_ERR_TIMEOUT", -5: "BSVD_ERR_NOT_IMPLEMENTED", -6: "BSVD_ERR_NOMEM"}
-PATHS = {"auto": 0, "fused": 1, "plain": 2, "blocked": 3}
+PATHS = {"auto": 0, "fused": 1, "plain": 2, "blocked": 3, "persistent": 4}
 FLAG_NO_V_CORRECTION, FLAG_TWO_STAGE, FLAG_NO_MASKS = 1, 2, 4
 DTYPES = {torch.float32: "s", torch.float64: "d", torch.complex64: "c", torch.complex128: "z"}
 REAL = {torch.float32: torch.float32, torch.float64: torch.float64,

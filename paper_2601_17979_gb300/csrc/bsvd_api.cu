@@ -71,7 +71,7 @@ bool resolve(const bsvd_opts* o, bool single, int N, Resolved& r) {
     std::memset(&z, 0, sizeof z);
     if (!o) o = &z;
     if (o->nb < 0 || o->max_sweeps < 0 || o->inner_sweeps < 0 || o->tol < 0 || o->path < 0 ||
-        o->path > BSVD_PATH_BLOCKED || o->flags < 0 || o->flags > 7 || o->prec < 0 ||
+        o->path > BSVD_PATH_PERSISTENT || o->flags < 0 || o->flags > 7 || o->prec < 0 ||
         o->prec > BSVD_PREC_MIXED || (o->prec == BSVD_PREC_MIXED && single))
         return false;
     r.nb = o->nb ? o->nb : (N >= 48 ? 16 : (N >= 12 ? 8 : 4));
@@ -88,6 +88,8 @@ bool resolve(const bsvd_opts* o, bool single, int N, Resolved& r) {
 typedef size_t (*plan_fn)(int, int, int, bool, FusedArgs&, int&);
 typedef cudaError_t (*launch_fn)(int, const FusedArgs&, int, size_t, cudaStream_t);
 typedef cudaError_t (*blocked_fn)(int, const BlockedArgs&, void*, cudaStream_t, bool, bool);
+typedef cudaError_t (*persist_fn)(int, const bsvd::PersistArgs&, int, int, cudaStream_t);
+typedef long long (*slot_fn)(int, int, int);
 
 struct TypeOps {
     bool single;
@@ -95,14 +97,20 @@ struct TypeOps {
     plan_fn plan;
     launch_fn launch;
     blocked_fn blocked;
+    persist_fn persist;
+    slot_fn slot;
 };
 
 TypeOps ops_for(char t) {
     switch (t) {
-        case 's': return {true, 4, bsvd::fused_plan_s, bsvd::fused_launch_s, bsvd::blocked_run_s};
-        case 'd': return {false, 8, bsvd::fused_plan_d, bsvd::fused_launch_d, bsvd::blocked_run_d};
-        case 'c': return {true, 8, bsvd::fused_plan_c, bsvd::fused_launch_c, bsvd::blocked_run_c};
-        default:  return {false, 16, bsvd::fused_plan_z, bsvd::fused_launch_z, bsvd::blocked_run_z};
+        case 's': return {true, 4, bsvd::fused_plan_s, bsvd::fused_launch_s, bsvd::blocked_run_s,
+                          bsvd::persist_launch_s, bsvd::persist_slot_s};
+        case 'd': return {false, 8, bsvd::fused_plan_d, bsvd::fused_launch_d, bsvd::blocked_run_d,
+                          bsvd::persist_launch_d, bsvd::persist_slot_d};
+        case 'c': return {true, 8, bsvd::fused_plan_c, bsvd::fused_launch_c, bsvd::blocked_run_c,
+                          bsvd::persist_launch_c, bsvd::persist_slot_c};
+        default:  return {false, 16, bsvd::fused_plan_z, bsvd::fused_launch_z, bsvd::blocked_run_z,
+                          bsvd::persist_launch_z, bsvd::persist_slot_z};
     }
 }
 
@@ -323,6 +331,7 @@ bsvd_status strided_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
     const TypeOps ops = ops_for(t);
     Resolved r;
     if (!resolve(opts, ops.single, k, r)) return fail_arg(h, 22);
+    if (r.path == BSVD_PATH_PERSISTENT) r.path = BSVD_PATH_AUTO;   // one shape: the regular paths
     if (batch == 0) return BSVD_OK;
     bsvd_status st = refresh_device(h);
     if (st != BSVD_OK) return st;
@@ -385,6 +394,103 @@ bsvd_status plan_batched(int max_smem, const TypeOps& ops, int batch, const Grou
     return BSVD_OK;
 }
 
+// ---- one persistent launch for a pointer-array batch of any shapes -----------
+struct PersistPlan {
+    int nb = 0, grid = 0, maxN = 0, count = 0;
+    long long slot = 0;
+    std::vector<int> order;     // non-empty ids, largest first
+    size_t ints = 0, bytes = 0;
+};
+
+int device_sms_or_default(bsvd_handle h) {
+    int dev = 0, v = 0;
+    if (h->device >= 0) return h->sm_count;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+        return v;
+    cudaGetLastError();
+    return 152;   // GB300
+}
+
+bsvd_status plan_persistent(int sms, const TypeOps& ops, int batch, const int* m, const int* n,
+                            const bsvd_opts* opts, PersistPlan& pp) {
+    pp.maxN = 0;
+    pp.order.clear();
+    for (int i = 0; i < batch; ++i) {
+        const int k = std::min(m[i], n[i]);
+        if (k > 0) pp.order.push_back(i);
+        pp.maxN = std::max(pp.maxN, k);
+    }
+    // largest first: cost ~ M N^2 per sweep
+    std::stable_sort(pp.order.begin(), pp.order.end(), [&](int a, int b) {
+        const double ca = (double)std::max(m[a], n[a]) * std::min(m[a], n[a]) * std::min(m[a], n[a]);
+        const double cb = (double)std::max(m[b], n[b]) * std::min(m[b], n[b]) * std::min(m[b], n[b]);
+        return ca > cb;
+    });
+    pp.count = (int)pp.order.size();
+    const int nbo = opts ? opts->nb : 0;
+    pp.nb = nbo ? nbo : (pp.maxN >= 48 ? 16 : (pp.maxN >= 12 ? 8 : 4));
+    if (!fused_nb(pp.nb)) return BSVD_ERR_NOT_IMPLEMENTED;
+    pp.slot = 0;
+    for (int id : pp.order) pp.slot = std::max(pp.slot, ops.slot(pp.nb, m[id], n[id]));
+    pp.grid = std::max(1, std::min(pp.count, sms * (ops.single ? 2 : 1)));
+    pp.ints = align256((size_t)(6 * (size_t)batch + 1) * sizeof(int));
+    pp.bytes = pp.ints + align256((size_t)pp.grid * pp.slot * ops.elt);
+    return BSVD_OK;
+}
+
+bsvd_status persistent_impl(bsvd_handle h, const TypeOps& ops, bool wantU, bool wantV, int batch,
+                            const int* m, const int* n, const void* const* dA, const int* lda,
+                            void* const* dS, void* const* dU, const int* ldu, void* const* dV,
+                            const int* ldv, int* d_info, int* d_sweeps, void* d_work,
+                            size_t work_bytes, const bsvd_opts* opts, cudaStream_t s) {
+    PersistPlan pp;
+    bsvd_status st = plan_persistent(h->sm_count, ops, batch, m, n, opts, pp);
+    if (st != BSVD_OK) return st;
+    if (!d_work || work_bytes < pp.bytes) return BSVD_ERR_WORKSPACE;
+    Resolved r;
+    if (!resolve(opts, ops.single, pp.maxN, r)) return fail_arg(h, 18);
+    // ints: lda, ldu, ldv, m, n, order (batch each), then the queue head
+    std::vector<int> host((size_t)6 * batch + 1, 0);
+    for (int i = 0; i < batch; ++i) {
+        host[i] = lda[i];
+        host[batch + i] = wantU ? ldu[i] : 1;
+        host[2 * (size_t)batch + i] = wantV ? ldv[i] : 1;
+        host[3 * (size_t)batch + i] = m[i];
+        host[4 * (size_t)batch + i] = n[i];
+    }
+    std::copy(pp.order.begin(), pp.order.end(), host.begin() + 5 * (size_t)batch);
+    int* dws = static_cast<int*>(d_work);
+    cudaError_t e = cudaMemcpyAsync(dws, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    for (int i = 0; i < batch; ++i)
+        if (std::min(m[i], n[i]) == 0) {
+            e = cudaMemsetAsync(d_info + i, 0, sizeof(int), s);
+            if (e == cudaSuccess && d_sweeps) e = cudaMemsetAsync(d_sweeps + i, 0, sizeof(int), s);
+            if (e != cudaSuccess) return fail_cuda(h, e);
+        }
+    if (pp.count == 0) return BSVD_OK;
+    bsvd::PersistArgs p;
+    std::memset(&p, 0, sizeof p);
+    FusedArgs& a = p.base;
+    a.Ap = dA; a.ldap = dws;
+    a.Sp = dS;
+    a.Up = dU; a.ldup = dws + batch;
+    a.Vp = dV; a.ldvp = dws + 2 * batch;
+    a.info = d_info; a.sweeps = d_sweeps;
+    a.wantU = wantU; a.wantV = wantV;
+    a.tol = r.tol; a.max_sweeps = r.max_sweeps; a.inner_sweeps = r.inner_sweeps; a.flags = r.flags;
+    p.mm = dws + 3 * batch;
+    p.nn = dws + 4 * batch;
+    p.order = dws + 5 * batch;
+    p.count = pp.count;
+    p.head = dws + 6 * batch;
+    p.ws = static_cast<char*>(d_work) + pp.ints;
+    p.slot_elems = pp.slot;
+    e = ops.persist(pp.nb, p, pp.grid, pp.maxN, s);
+    return e == cudaSuccess ? BSVD_OK : fail_cuda(h, e);
+}
+
 bsvd_status batched_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, int batch,
                          const int* m, const int* n, const void* const* dA, const int* lda,
                          void* const* dS, void* const* dU, const int* ldu, void* const* dV,
@@ -415,6 +521,12 @@ bsvd_status batched_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
     if (d_work && (reinterpret_cast<uintptr_t>(d_work) & 15) != 0) return fail_arg(h, 16);
     const TypeOps ops = ops_for(t);
     if (opts && opts->prec == BSVD_PREC_MIXED) return BSVD_ERR_NOT_IMPLEMENTED;   // strided form only
+    if (opts && opts->path == BSVD_PATH_PERSISTENT) {
+        bsvd_status st = refresh_device(h);
+        if (st != BSVD_OK) return st;
+        return persistent_impl(h, ops, wantU, wantV, batch, m, n, dA, lda, dS, dU, ldu, dV, ldv, d_info,
+                               d_sweeps, d_work, work_bytes, opts, static_cast<cudaStream_t>(stream));
+    }
     Groups groups;
     for (int i = 0; i < batch; ++i) groups[{m[i], n[i]}].push_back(i);
     // plan every group before touching the device, so a bad shape fails cleanly
@@ -547,6 +659,7 @@ bsvd_status bsvd_gesvj_workspace(bsvd_handle handle, char dtype, int batch, cons
         if (std::min(m, n) == 0) return BSVD_OK;
         Resolved r;
         if (!resolve(opts, ops.single, std::min(m, n), r)) return fail_arg(handle, 9);
+        if (r.path == BSVD_PATH_PERSISTENT) r.path = BSVD_PATH_AUTO;   // as the strided call does
         if (r.prec == BSVD_PREC_MIXED) {
             MixedPlan mp;
             bsvd_status st = plan_mixed(max_smem, dtype, m, n, batch, wantU, wantV, r, mp);
@@ -566,6 +679,12 @@ bsvd_status bsvd_gesvj_workspace(bsvd_handle handle, char dtype, int batch, cons
         groups[{m_arr[i], n_arr[i]}].push_back(i);
     }
     if (opts && opts->prec == BSVD_PREC_MIXED) return BSVD_ERR_NOT_IMPLEMENTED;   // strided form only
+    if (opts && opts->path == BSVD_PATH_PERSISTENT) {
+        PersistPlan pp;
+        bsvd_status st = plan_persistent(device_sms_or_default(handle), ops, batch, m_arr, n_arr, opts, pp);
+        if (st == BSVD_OK) *bytes = pp.bytes;
+        return st;
+    }
     std::vector<Plan> plans;
     std::vector<Resolved> res;
     bsvd_status st = plan_batched(max_smem, ops, batch, groups, wantU, wantV, opts, plans, res, *bytes);

@@ -2,6 +2,8 @@
 // instantiated once per scalar type by fused_{s,d,c,z}.cu.
 #pragma once
 
+#include <type_traits>
+
 #include "gesvj_fused.cuh"
 #include "internal.h"
 
@@ -20,13 +22,7 @@ template <class T, int NB>
 size_t fused_plan_nb(int M, int N, bool needVs, FusedArgs& a, int& nthreads) {
     using C = FusedCfg<NB>;
     using R = Real<T>;
-    const int l = N > 2 * NB ? (N + NB - 1) / NB : 2;
-    a.l = l;
-    a.L = l + (l & 1);
-    a.Np = l * NB;
-    a.ldw = M | 1;
-    a.ldvs = N | 1;
-    a.lde = N | 1;
+    fused_dims<T, NB>(M, N, a);    // (M, N): the working orientation
     size_t off = 0;
     a.offW = 0;
     off = align16((size_t)a.ldw * a.Np * sizeof(T));
@@ -50,6 +46,63 @@ size_t fused_plan(int nb, int M, int N, bool needVs, FusedArgs& a, int& nthreads
         case 8: return fused_plan_nb<T, 8>(M, N, needVs, a, nthreads);
         case 16: return fused_plan_nb<T, 16>(M, N, needVs, a, nthreads);
         default: return 0;
+    }
+}
+
+// Shared memory of the persistent kernel: the groups' Gram/rotation scratch and
+// the per-matrix flags sized for the largest N of the batch.
+template <class T, int NB>
+size_t persist_smem_nb(int maxN, FusedArgs& a, int& nthreads) {
+    using C = FusedCfg<NB>;
+    using R = Real<T>;
+    a.offW = a.offV = 0;
+    a.offG = 0;
+    a.groupBytes = fused_group_bytes<T, NB>();
+    size_t off = (size_t)C::NG * a.groupBytes;
+    a.offMisc = (int)off;
+    const int NT = C::NG * C::GT, NW = NT / 32;
+    off += kMaxSweeps * 4 + 16 + 2 * sizeof(T);
+    off += (size_t)((NW + 3) & ~3) * sizeof(R) + (size_t)((maxN + 3) & ~3) * sizeof(R) + (size_t)maxN * 4;
+    nthreads = NT;
+    return align16(off);
+}
+
+template <class T, int NB>
+cudaError_t persist_launch_nb(const PersistArgs& p, int grid, size_t smem, cudaStream_t st) {
+    using C = FusedCfg<NB>;
+    auto k = gesvj_persistent_kernel<T, NB, C::NG, C::GT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, C::NG * C::GT, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+// Slot elements for matrix (m, n) with block width NB.
+template <class T, int NB>
+long long persist_slot_nb(int m, int n) {
+    FusedArgs a;
+    fused_dims<T, NB>(m, n, a);
+    return fused_slot_elems<T>(a);
+}
+
+template <class T>
+cudaError_t persist_launch(int nb, PersistArgs p, int grid, int maxN, cudaStream_t st) {
+    int nt = 0;
+    switch (nb) {
+        case 4: { size_t sm = persist_smem_nb<T, 4>(maxN, p.base, nt); return persist_launch_nb<T, 4>(p, grid, sm, st); }
+        case 8: { size_t sm = persist_smem_nb<T, 8>(maxN, p.base, nt); return persist_launch_nb<T, 8>(p, grid, sm, st); }
+        case 16: { size_t sm = persist_smem_nb<T, 16>(maxN, p.base, nt); return persist_launch_nb<T, 16>(p, grid, sm, st); }
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class T>
+long long persist_slot(int nb, int m, int n) {
+    switch (nb) {
+        case 4: return persist_slot_nb<T, 4>(m, n);
+        case 8: return persist_slot_nb<T, 8>(m, n);
+        case 16: return persist_slot_nb<T, 16>(m, n);
+        default: return -1;
     }
 }
 
@@ -80,6 +133,11 @@ cudaError_t fused_launch(int nb, const FusedArgs& a, int grid, size_t smem, cuda
     size_t bsvd::fused_plan_##TAG(int nb, int M, int N, bool needVs, FusedArgs& a, int& nt) { \
         return fused_plan<TYPE>(nb, M, N, needVs, a, nt);                                    \
     }                                                                                        \
+    cudaError_t bsvd::persist_launch_##TAG(int nb, const PersistArgs& p, int grid, int maxN,  \
+                                           cudaStream_t st) {                                \
+        return persist_launch<TYPE>(nb, p, grid, maxN, st);                                  \
+    }                                                                                        \
+    long long bsvd::persist_slot_##TAG(int nb, int m, int n) { return persist_slot<TYPE>(nb, m, n); } \
     cudaError_t bsvd::fused_launch_##TAG(int nb, const FusedArgs& a, int grid, size_t smem,  \
                                          cudaStream_t st) {                                  \
         return fused_launch<TYPE>(nb, a, grid, smem, st);                                    \

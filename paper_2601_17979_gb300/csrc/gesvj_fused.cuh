@@ -18,6 +18,9 @@
 // orthogonality V loses over many J products.
 #pragma once
 
+#include <type_traits>
+
+#include "fused_f32.cuh"
 #include "jacobi_common.cuh"
 
 namespace bsvd {
@@ -48,30 +51,76 @@ struct FusedArgs {
 enum : int { kFlagNoVCorrection = 1 };
 
 // Shared-memory bytes of one thread group's scratch (G, J, rotation table).
+// Working shape and leading dimensions of one matrix: M >= N (A^H when
+// m < n), l >= 2 blocks of NB columns (padded), and for FP32 16-byte aligned
+// columns (an odd multiple of 4 floats) for the float4 tiles, for the other
+// types an odd leading dimension (different columns in different banks).
 template <class T, int NB>
-__host__ __device__ constexpr int fused_group_bytes() {
-    return (2 * (2 * NB) * (2 * NB + 1) * (int)sizeof(T) + InnerTables<T, NB>::bytes() + 15) & ~15;
+__host__ __device__ inline void fused_dims(int m, int n, FusedArgs& a) {
+    a.m = m;
+    a.n = n;
+    a.trans = m < n;
+    a.M = m < n ? n : m;
+    a.N = m < n ? m : n;
+    const int M = a.M, N = a.N;
+    const int l = N > 2 * NB ? (N + NB - 1) / NB : 2;
+    a.l = l;
+    a.L = l + (l & 1);
+    a.Np = l * NB;
+    if (std::is_same<T, float>::value) {
+        a.ldw = (M + 3) & ~3;
+        if (a.ldw % 8 == 0) a.ldw += 4;
+        a.ldvs = (N + 3) & ~3;
+    } else {
+        a.ldw = M | 1;
+        a.ldvs = N | 1;
+    }
+    a.lde = ((long long)(N | 1) * N <= (long long)a.ldw * a.Np) ? (N | 1) : N;
 }
 
+// Elements of the W + V working arrays of one matrix (V after W at a 16-byte
+// boundary), for a global-memory slot.
+template <class T>
+__host__ __device__ inline long long fused_slot_elems(const FusedArgs& a) {
+    const long long per16 = 16 / (long long)sizeof(T) > 0 ? 16 / (long long)sizeof(T) : 1;
+    const long long w = ((long long)a.ldw * a.Np + per16 - 1) / per16 * per16;
+    return w + (long long)a.ldvs * a.Np;
+}
+
+// FP32 adds J^T (2nb x 2nb, 16-byte aligned) for the tiled update.
+template <class T, int NB>
+__host__ __device__ constexpr int fused_group_bytes() {
+    return ((2 * (2 * NB) * (2 * NB + 1) * (int)sizeof(T) + InnerTables<T, NB>::bytes() + 15) & ~15) +
+           (std::is_same<T, float>::value ? (2 * NB) * (2 * NB) * 4 : 0);
+}
+
+// Real FP32 keeps two CTAs per SM (its shared memory allows them).
+template <class T>
+constexpr int fused_min_blocks() { return std::is_same<T, float>::value ? 2 : 1; }
+
+// The whole solve of matrix `mid` by one CTA: load, sweeps, finalise.  W
+// (ldw x Np) and Vs (ldvs x Np) are the working arrays -- shared memory for
+// the on-chip kernel, a global-memory slot for the persistent one; the Gram
+// blocks, rotation tables and flags are always in shared memory at the
+// offsets of `a`.  All threads of the CTA call it and return together.
 template <class T, int NB, int NG, int GT>
-__global__ void __launch_bounds__(NG * GT)
-gesvj_fused_kernel(const FusedArgs a) {
+__device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T* const W, T* const Vs,
+                                            unsigned char* const smem) {
     using R = Real<T>;
     constexpr int TWO = 2 * NB, LDG = TWO + 1, NT = NG * GT, NW = NT / 32;
-    extern __shared__ __align__(16) unsigned char smem[];
 
     const int tid = threadIdx.x, g = tid / GT, gt = tid % GT, lane = tid & 31, warp = tid >> 5;
-    const int mid = a.index ? a.index[blockIdx.x] : (int)blockIdx.x;
     const int M = a.M, N = a.N, ldw = a.ldw, ldvs = a.ldvs;
     const bool needVs = a.trans ? a.wantU : a.wantV;   // V is part of the output
     const bool wantWout = a.trans ? a.wantV : a.wantU; // W / sigma is part of the output
 
-    T* W = reinterpret_cast<T*>(smem + a.offW);
-    T* Vs = reinterpret_cast<T*>(smem + a.offV);
     unsigned char* gb = smem + a.offG + g * a.groupBytes;
     T* G = reinterpret_cast<T*>(gb);
     T* J = G + TWO * LDG;
     const InnerTables<T, NB> tb(J + TWO * LDG);
+    // J^T for the FP32 tiled update: after the tables, 16-byte aligned
+    float* Jt = reinterpret_cast<float*>(
+        gb + ((2 * TWO * LDG * (int)sizeof(T) + InnerTables<T, NB>::bytes() + 15) & ~15));
     int* swflag = reinterpret_cast<int*>(smem + a.offMisc);   // [kMaxSweeps] per-sweep "rotated"
     int* iscr = swflag + kMaxSweeps;                           // [4]: 0 bad input, 1 pivot row
     T* bcast = reinterpret_cast<T*>(iscr + 4);                 // [2] broadcast slot
@@ -93,6 +142,10 @@ gesvj_fused_kernel(const FusedArgs a) {
         else         W[i + j * ldw] = x;
     }
     for (int e = tid; e < M * (a.Np - N); e += NT) W[(e % M) + (N + e / M) * ldw] = make_s<T>(0);
+    if (ldw > M)   // rows M..ldw-1 (read, never used, by the FP32 tiles)
+        for (int e = tid; e < (ldw - M) * a.Np; e += NT) W[M + e % (ldw - M) + (e / (ldw - M)) * ldw] = make_s<T>(0);
+    if (needVs && ldvs > N)
+        for (int e = tid; e < (ldvs - N) * a.Np; e += NT) Vs[N + e % (ldvs - N) + (e / (ldvs - N)) * ldvs] = make_s<T>(0);
     if (needVs) {
         const T* V0 = a.V0 ? static_cast<const T*>(a.V0) + (long long)mid * a.sV0 : nullptr;
         for (int e = tid; e < N * a.Np; e += NT) {
@@ -163,7 +216,10 @@ gesvj_fused_kernel(const FusedArgs a) {
                 // S2: G = P^H P, upper triangle, mirrored to keep G Hermitian.
                 // Lanes l and l+16 of a warp sum the same entry over the two
                 // halves of the rows [0, M/2) and [M/2, M); one shuffle adds them.
-                {
+                // FP32: register-tiled (fused_f32.cuh).
+                if constexpr (std::is_same<T, float>::value) {
+                    gram_f32_tiled<NB, GT>(W, ldw, M, bi * NB, bj * NB, G, gt);
+                } else {
                     constexpr int NUP = TWO * (TWO + 1) / 2, NWG = GT / 32;
                     const int wg = gt >> 5, kh = (gt >> 4) & 1, el = gt & 15;
                     const int kb = kh ? M / 2 : 0, ke = kh ? M : M / 2;
@@ -195,8 +251,12 @@ gesvj_fused_kernel(const FusedArgs a) {
                 // S4/S5: [W_i W_j] <- [W_i W_j] J and [V_i V_j] <- [V_i V_j] J.
                 // A warp takes 16 rows at a time; lanes l and l+16 both read row
                 // l and write the first and the second nb outputs of it, so the
-                // M + n rows spread evenly over the group.
-                {
+                // M + n rows spread evenly over the group.  FP32: register tiles.
+                if constexpr (std::is_same<T, float>::value) {
+                    for (int e = gt; e < TWO * TWO; e += GT) Jt[(e / TWO) + (e % TWO) * TWO] = J[(e % TWO) + (e / TWO) * LDG];
+                    group_sync(g, GT);
+                    update_f32_tiled<NB, GT, 2>(W, ldw, ldw, Vs, ldvs, needVs ? ldvs : 0, bi * NB, bj * NB, Jt, gt, g + 1);
+                } else {
                     const int rows = M + (needVs ? N : 0);
                     const int wg = gt >> 5, half = (gt >> 4) & 1, rl = gt & 15;
                     constexpr int NWG = GT / 32;
@@ -247,6 +307,55 @@ gesvj_fused_kernel(const FusedArgs a) {
     if (tid == 0) {
         a.info[mid] = converged ? 0 : sw;
         if (a.sweeps) a.sweeps[mid] = sw;
+    }
+}
+
+template <class T, int NB, int NG, int GT>
+__global__ void __launch_bounds__(NG * GT, fused_min_blocks<T>())
+gesvj_fused_kernel(const FusedArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int mid = a.index ? a.index[blockIdx.x] : (int)blockIdx.x;
+    fused_solve<T, NB, NG, GT>(a, mid, reinterpret_cast<T*>(smem + a.offW), reinterpret_cast<T*>(smem + a.offV),
+                               smem);
+}
+
+// Pointer-array batches of any shapes in one persistent launch: each CTA
+// takes the next matrix from a work queue (ids in `order`, largest first),
+// lays it out in its own global-memory slot and solves it with the same
+// per-matrix code as the on-chip kernel.
+struct PersistArgs {
+    FusedArgs base;            // outputs, options, jobs and shared-memory offsets
+    const int* mm;             // m of each matrix (by id)
+    const int* nn;             // n of each matrix (by id)
+    const int* order;          // queue of ids
+    int count;                 // queue length
+    int* head;                 // queue head, zero at launch
+    void* ws;                  // gridDim.x slots of slot_elems elements
+    long long slot_elems;
+};
+
+template <class T, int NB, int NG, int GT>
+__global__ void __launch_bounds__(NG * GT, fused_min_blocks<T>())
+gesvj_persistent_kernel(const PersistArgs p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_mid;
+    T* const slot = static_cast<T*>(p.ws) + (long long)blockIdx.x * p.slot_elems;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int k = atomicAdd(p.head, 1);
+            s_mid = k < p.count ? p.order[k] : -1;
+        }
+        __syncthreads();
+        const int mid = s_mid;
+        __syncthreads();                                   // all have read s_mid
+        if (mid < 0) break;
+        FusedArgs a = p.base;
+        fused_dims<T, NB>(p.mm[mid], p.nn[mid], a);
+        const long long per16 = 16 / (long long)sizeof(T) > 0 ? 16 / (long long)sizeof(T) : 1;
+        T* const W = slot;
+        T* const Vs = slot + ((long long)a.ldw * a.Np + per16 - 1) / per16 * per16;
+        fused_solve<T, NB, NG, GT>(a, mid, W, Vs, smem);
+        __syncthreads();                                   // shared scratch reused next
     }
 }
 

@@ -9,6 +9,7 @@ namespace bsvd {
 
 struct FusedArgs;
 struct BlockedArgs;
+struct PersistArgs;
 
 // Buffers of the mixed-precision path (strided batches; per matrix, in the
 // working orientation M = max(m, n) rows, N = min(m, n) columns).
@@ -33,7 +34,10 @@ size_t blocked_bytes(int nb, int M, int N, int count, bool two_stage, size_t elt
 #define BSVD_DECLARE_FUSED(TAG)                                                          \
     size_t fused_plan_##TAG(int nb, int M, int N, bool needVs, FusedArgs& a, int& nt);  \
     cudaError_t fused_launch_##TAG(int nb, const FusedArgs& a, int grid, size_t smem,   \
-                                   cudaStream_t st);
+                                   cudaStream_t st);                                    \
+    cudaError_t persist_launch_##TAG(int nb, const PersistArgs& p, int grid, int maxN,  \
+                                     cudaStream_t st);                                  \
+    long long persist_slot_##TAG(int nb, int m, int n);
 
 #define BSVD_DECLARE_BLOCKED(TAG)                                                               \
     cudaError_t blocked_run_##TAG(int nb, const BlockedArgs& a, void* work, cudaStream_t st,   \

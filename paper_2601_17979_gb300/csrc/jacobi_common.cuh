@@ -62,134 +62,237 @@ __device__ __forceinline__ double warp_sum_s(double v) { return warp_sum(v); }
 __device__ __forceinline__ float2 warp_sum_s(float2 v) { return make_float2(warp_sum(v.x), warp_sum(v.y)); }
 __device__ __forceinline__ double2 warp_sum_s(double2 v) { return make_double2(warp_sum(v.x), warp_sum(v.y)); }
 
-// Rotation table of one inner step (nb disjoint rotations) plus a counter of
-// fired rotations, laid out in shared memory right after J.
+// Rotation tables of the inner solver: two steps' worth (double-buffered, so
+// the next step's rotations can be formed while the current step's are still
+// being applied) of nb disjoint rotations -- c, t = tan(theta), e s with
+// e = e^{i phi}, the index pair and a fired flag -- plus one fired-rotation
+// counter per sweep parity.  Laid out in shared memory right after J.
 template <class T, int NB>
 struct InnerTables {
     using R = Real<T>;
-    R* c; R* s; R* t; T* ph; int* p; int* q; int* fired; int* count;
+    struct Step { R* c; R* t; T* es; int* p; int* q; int* fired; };
+    Step step[2];
+    int* count;   // [2]
     __device__ explicit InnerTables(void* base) {
-        c = static_cast<R*>(base);
-        s = c + NB;
-        t = s + NB;
-        ph = reinterpret_cast<T*>(t + NB);
-        p = reinterpret_cast<int*>(ph + NB);
-        q = p + NB;
-        fired = q + NB;
-        count = fired + NB;
+        char* b = static_cast<char*>(base);
+        for (int k = 0; k < 2; ++k) {
+            step[k].es = reinterpret_cast<T*>(b);  b += NB * sizeof(T);
+            step[k].c = reinterpret_cast<R*>(b);   b += NB * sizeof(R);
+            step[k].t = reinterpret_cast<R*>(b);   b += NB * sizeof(R);
+            step[k].p = reinterpret_cast<int*>(b); b += NB * sizeof(int);
+            step[k].q = reinterpret_cast<int*>(b); b += NB * sizeof(int);
+            step[k].fired = reinterpret_cast<int*>(b); b += NB * sizeof(int);
+        }
+        count = reinterpret_cast<int*>(b);
     }
     __host__ __device__ static constexpr int bytes() {
-        return NB * (3 * (int)sizeof(R) + (int)sizeof(T)) + NB * 3 * 4 + 16;
+        return 2 * NB * ((int)sizeof(T) + 2 * (int)sizeof(Real<T>) + 3 * 4) + 16;
     }
 };
+
+// Below this, g_pp g_qq is not squared-compared (its square could underflow).
+template <class R> constexpr R kJacobiProdMin = R(0);
+template <> constexpr float kJacobiProdMin<float> = 1e-30f;
+template <> constexpr double kJacobiProdMin<double> = 1e-280;
+
+// t = sign(x) y / (|x| + hypot(x, y)), y > 0.  FP32: sqrt and a fast division
+// (a couple of ulp) within the range where x^2 + y^2 neither overflows nor
+// underflows -- any t close to the exact one gives an orthogonal rotation,
+// since c = 1/sqrt(1 + t^2) and s = t c.  FP64: IEEE hypot and division.
+__device__ __forceinline__ float rotation_tan(float x, float y) {
+    const float ax = fabsf(x), m = fmaxf(ax, y);
+    const float h = (m > 1e-18f && m < 1e18f) ? sqrtf(fmaf(x, x, y * y)) : hypotf(x, y);
+    const float yy = x >= 0.f ? y : -y;
+    return (m > 1e-18f && m < 1e18f) ? __fdividef(yy, ax + h) : yy / (ax + h);
+}
+__device__ __forceinline__ double rotation_tan(double x, double y) {
+    return (x >= 0 ? y : -y) / (fabs(x) + hypot(x, y));
+}
+
+// One thread's rotation for slot `slot` of round-robin step `st` on the 2NB
+// indices: test |g_pq| >= tol sqrt(g_pp) sqrt(g_qq) (Alg. 1) and form
+// (c, s, e^{i phi}) by Eq. (sin-cos) with sign(0) = +1.  Returns fired.
+template <class T, int NB>
+__device__ __forceinline__ int inner_rotation(const T* G, Real<T> tol, int st, int slot,
+                                              const typename InnerTables<T, NB>::Step& out) {
+    using R = Real<T>;
+    constexpr int TWO = 2 * NB, LDG = TWO + 1;
+    int p, q;
+    rr_pair(TWO, st, slot, p, q);
+    const R gpp = re(G[p + p * LDG]), gqq = re(G[q + q * LDG]);
+    const T gpq = G[p + q * LDG];
+    const R apq = abs_s(gpq);
+    // |g_pq| >= tol sqrt(g_pp) sqrt(g_qq), compared in squares while the
+    // product stays well inside the normal range
+    const R prod = gpp * gqq;
+    const bool fire = gpp > 0 && gqq > 0 && apq > 0 &&
+                      (prod > kJacobiProdMin<R> ? apq * apq >= tol * tol * prod
+                                                : apq >= tol * sqrt_r(gpp) * sqrt_r(gqq));
+    R c = 1, t = 0;
+    T es = make_s<T>(0);
+    if (fire) {
+        // tau = x / y with x = g_pp - g_qq, y = 2 |g_pq|:
+        // t = sign(tau) / (|tau| + sqrt(1 + tau^2)) = sign(x) y / (|x| + hypot(x, y))
+        const R x = gpp - gqq, y = 2 * apq;
+        t = rotation_tan(x, y);
+        c = rsqrt_r(R(1) + t * t);
+        es = scale(phase_s(gpq, apq), t * c);
+    }
+    out.c[slot] = c; out.t[slot] = t; out.es[slot] = es;
+    out.p[slot] = p; out.q[slot] = q; out.fired[slot] = fire;
+    return fire;
+}
 
 // Up to `sweeps` sweeps of Alg. 1 on the Hermitian G (2NB x 2NB, leading
 // dimension 2NB+1, in shared memory), accumulating the rotations into J
 // (set to I here).  One sweep is 2NB-1 parallel steps of the round-robin
-// ordering on the 2NB indices; in each, NB threads test their pair
-// (|g_pq| >= tol sqrt(g_pp) sqrt(g_qq), Alg. 1) and compute (c, s, e^{i phi})
-// by Eq. (sin-cos) with sign(0) = +1; then G <- R^H G R is applied as 2x2
-// block transforms (rows of one slot, columns of another; the diagonal
-// block by the closed form g_pp += t|g_pq|, g_qq -= t|g_pq|, g_pq = 0) and
-// J <- J R.  Sweeps stop early once one rotates nothing.
-// Executed by GT threads (index gt) that share named barrier `bar`.  The
-// caller must have finished writing G and synchronised.  Returns the number
-// of rotations fired (0: G was diagonal to tol); uniform over the group.
+// ordering on the 2NB indices, each applying nb disjoint rotations:
+// G <- R^H G R as 2x2 block transforms (rows of one slot, columns of another;
+// the diagonal block by the closed form g_pp += t|g_pq|, g_qq -= t|g_pq|,
+// g_pq = 0) and J <- J R.  Pipelined: while the other warps apply step s to
+// J, warp 0 already forms the rotations of step s+1 from the updated G.
+// Sweeps stop early once one rotates nothing.  Executed by GT threads (index
+// gt) sharing named barrier `bar`; the caller must have finished writing G and
+// synchronised.  Returns the number of rotations fired (0: G was diagonal to
+// tol); uniform over the group.
 template <class T, int NB, int GT>
 __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> tol, int sweeps,
                             int gt, int bar) {
     using R = Real<T>;
-    constexpr int TWO = 2 * NB, LDG = TWO + 1;
+    constexpr int TWO = 2 * NB, LDG = TWO + 1, STEPS = TWO - 1;
+    constexpr int NBLK = NB * (NB + 1) / 2, NBU = (NBLK + GT - 1) / GT;
+    // J-update workers: every warp but the first when there is more than one
+    constexpr int JW0 = GT > 32 ? 32 : 0, JWN = GT - JW0;
+    int bq1[NBU], bq2[NBU];
+#pragma unroll
+    for (int u = 0; u < NBU; ++u) {
+        const int e = gt + u * GT;
+        if (e < NBLK) tri_index(e, bq1[u], bq2[u]);
+        else { bq1[u] = -1; bq2[u] = -1; }
+    }
     for (int e = gt; e < TWO * TWO; e += GT)
         J[(e % TWO) + (e / TWO) * LDG] = make_s<T>((e % TWO) == (e / TWO) ? 1 : 0);
-    if (gt == 0) *tb.count = 0;
+    if (gt == 0) { tb.count[0] = 0; tb.count[1] = 0; }
+    named_sync(bar, GT);
+    if (gt < 32) {   // warp 0 forms the rotations; one ballot counts the fired ones
+        const int f = gt < NB ? inner_rotation<T, NB>(G, tol, 0, gt, tb.step[0]) : 0;
+        const unsigned m = __ballot_sync(0xffffffffu, f);
+        if (gt == 0) tb.count[0] += __popc(m);
+    }
     named_sync(bar, GT);
     int seen = 0;
     for (int isw = 0; isw < sweeps; ++isw) {
-        for (int st = 0; st < TWO - 1; ++st) {
-            if (gt < NB) {
-                int p, q;
-                rr_pair(TWO, st, gt, p, q);
-                const R gpp = re(G[p + p * LDG]), gqq = re(G[q + q * LDG]);
-                const T gpq = G[p + q * LDG];
-                const R apq = abs_s(gpq);
-                const bool fire = gpp > 0 && gqq > 0 && apq > 0 && apq >= tol * sqrt_r(gpp) * sqrt_r(gqq);
-                R c = 1, sn = 0, t = 0;
-                T ph = make_s<T>(1);
-                if (fire) {
-                    // Eq. (sin-cos) with tau = x / y, x = g_pp - g_qq, y = 2 |g_pq|:
-                    // t = sign(tau) / (|tau| + sqrt(1 + tau^2)) = sign(x) y / (|x| + hypot(x, y))
-                    const R x = gpp - gqq, y = 2 * apq;
-                    t = (x >= 0 ? y : -y) / (fabs(x) + hypot_r(x, y));
-                    c = rsqrt_r(R(1) + t * t);
-                    sn = t * c;
-                    ph = phase_s(gpq, apq);
-                    atomicAdd(tb.count, 1);
+        for (int st = 0; st < STEPS; ++st) {
+            const int gs = isw * STEPS + st;
+            const auto& cur = tb.step[gs & 1];
+            // G <- R^H G R on 2x2 blocks (slot q1 <= slot q2), mirrored.  A
+            // thread's blocks are disjoint: all loads first, then the math,
+            // then the stores, so their latencies overlap.
+            {
+                int f1[NBU], f2[NBU], p1[NBU], r1[NBU], p2[NBU], r2[NBU];
+                R c1[NBU], c2[NBU], t1[NBU];
+                T e1[NBU], e2[NBU], b00[NBU], b01[NBU], b10[NBU], b11[NBU];
+#pragma unroll
+                for (int u = 0; u < NBU; ++u) {
+                    f1[u] = f2[u] = 0;
+                    if (bq1[u] < 0) continue;
+                    const int q1 = bq1[u], q2 = bq2[u];
+                    f1[u] = cur.fired[q1]; f2[u] = cur.fired[q2];
+                    p1[u] = cur.p[q1]; r1[u] = cur.q[q1]; p2[u] = cur.p[q2]; r2[u] = cur.q[q2];
+                    c1[u] = cur.c[q1]; c2[u] = cur.c[q2]; t1[u] = cur.t[q1];
+                    e1[u] = cur.es[q1]; e2[u] = cur.es[q2];
                 }
-                tb.c[gt] = c; tb.s[gt] = sn; tb.t[gt] = t; tb.ph[gt] = ph;
-                tb.p[gt] = p; tb.q[gt] = q; tb.fired[gt] = fire;
+#pragma unroll
+                for (int u = 0; u < NBU; ++u) {
+                    if (!f1[u] && !f2[u]) continue;
+                    b00[u] = G[p1[u] + p2[u] * LDG]; b01[u] = G[p1[u] + r2[u] * LDG];
+                    b10[u] = G[r1[u] + p2[u] * LDG]; b11[u] = G[r1[u] + r2[u] * LDG];
+                }
+#pragma unroll
+                for (int u = 0; u < NBU; ++u) {
+                    if (!f1[u] && !f2[u]) continue;
+                    if (bq1[u] == bq2[u]) {
+                        // diagonal block: closed form, off-diagonal set to zero
+                        const R apq = abs_s(b01[u]);
+                        b00[u] = make_s<T>(re(b00[u]) + t1[u] * apq);
+                        b11[u] = make_s<T>(re(b11[u]) - t1[u] * apq);
+                        b01[u] = make_s<T>(0);
+                        b10[u] = make_s<T>(0);
+                        continue;
+                    }
+                    if (f2[u]) {   // columns (p2, r2) times R2
+                        const T es = e2[u], ces = conj_s(es);
+                        const T n00 = add(scale(b00[u], c2[u]), mul(b01[u], ces));
+                        const T n01 = sub(scale(b01[u], c2[u]), mul(b00[u], es));
+                        const T n10 = add(scale(b10[u], c2[u]), mul(b11[u], ces));
+                        const T n11 = sub(scale(b11[u], c2[u]), mul(b10[u], es));
+                        b00[u] = n00; b01[u] = n01; b10[u] = n10; b11[u] = n11;
+                    }
+                    if (f1[u]) {   // rows (p1, r1) times R1^H
+                        const T es = e1[u], ces = conj_s(es);
+                        const T n00 = add(scale(b00[u], c1[u]), mul(es, b10[u]));
+                        const T n10 = sub(scale(b10[u], c1[u]), mul(ces, b00[u]));
+                        const T n01 = add(scale(b01[u], c1[u]), mul(es, b11[u]));
+                        const T n11 = sub(scale(b11[u], c1[u]), mul(ces, b01[u]));
+                        b00[u] = n00; b01[u] = n01; b10[u] = n10; b11[u] = n11;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < NBU; ++u) {
+                    if (!f1[u] && !f2[u]) continue;
+                    G[p1[u] + p2[u] * LDG] = b00[u]; G[p1[u] + r2[u] * LDG] = b01[u];
+                    G[r1[u] + p2[u] * LDG] = b10[u]; G[r1[u] + r2[u] * LDG] = b11[u];
+                    if (bq1[u] != bq2[u]) {
+                        G[p2[u] + p1[u] * LDG] = conj_s(b00[u]); G[r2[u] + p1[u] * LDG] = conj_s(b01[u]);
+                        G[p2[u] + r1[u] * LDG] = conj_s(b10[u]); G[r2[u] + r1[u] * LDG] = conj_s(b11[u]);
+                    }
+                }
             }
             named_sync(bar, GT);
-            // G <- R^H G R on 2x2 blocks (slot q1 <= slot q2), mirrored
-            constexpr int NBLK = NB * (NB + 1) / 2;
-            for (int e = gt; e < NBLK; e += GT) {
-                int q1, q2;
-                tri_index(e, q1, q2);
-                const bool f1 = tb.fired[q1], f2 = tb.fired[q2];
-                if (!f1 && !f2) continue;
-                const int p1 = tb.p[q1], r1 = tb.q[q1], p2 = tb.p[q2], r2 = tb.q[q2];
-                if (q1 == q2) {
-                    const R tt = tb.t[q1];
-                    const R apq = abs_s(G[p1 + r1 * LDG]);
-                    G[p1 + p1 * LDG] = make_s<T>(re(G[p1 + p1 * LDG]) + tt * apq);
-                    G[r1 + r1 * LDG] = make_s<T>(re(G[r1 + r1 * LDG]) - tt * apq);
-                    G[p1 + r1 * LDG] = make_s<T>(0);
-                    G[r1 + p1 * LDG] = make_s<T>(0);
-                    continue;
-                }
-                T b00 = G[p1 + p2 * LDG], b01 = G[p1 + r2 * LDG];
-                T b10 = G[r1 + p2 * LDG], b11 = G[r1 + r2 * LDG];
-                if (f2) {   // columns (p2, r2) times R2
-                    const R c2 = tb.c[q2];
-                    const T es = scale(tb.ph[q2], tb.s[q2]), ces = conj_s(es);
-                    const T n00 = add(scale(b00, c2), mul(b01, ces));
-                    const T n01 = sub(scale(b01, c2), mul(b00, es));
-                    const T n10 = add(scale(b10, c2), mul(b11, ces));
-                    const T n11 = sub(scale(b11, c2), mul(b10, es));
-                    b00 = n00; b01 = n01; b10 = n10; b11 = n11;
-                }
-                if (f1) {   // rows (p1, r1) times R1^H
-                    const R c1 = tb.c[q1];
-                    const T es = scale(tb.ph[q1], tb.s[q1]), ces = conj_s(es);
-                    const T n00 = add(scale(b00, c1), mul(es, b10));
-                    const T n10 = sub(scale(b10, c1), mul(ces, b00));
-                    const T n01 = add(scale(b01, c1), mul(es, b11));
-                    const T n11 = sub(scale(b11, c1), mul(ces, b01));
-                    b00 = n00; b01 = n01; b10 = n10; b11 = n11;
-                }
-                G[p1 + p2 * LDG] = b00; G[p1 + r2 * LDG] = b01;
-                G[r1 + p2 * LDG] = b10; G[r1 + r2 * LDG] = b11;
-                G[p2 + p1 * LDG] = conj_s(b00); G[r2 + p1 * LDG] = conj_s(b01);
-                G[p2 + r1 * LDG] = conj_s(b10); G[r2 + r1 * LDG] = conj_s(b11);
+            // warp 0: the rotations of the next step (this sweep, or the first
+            // step of the next one) from the updated G
+            const bool last = (st + 1 == STEPS);
+            if (gt < 32 && !(last && isw + 1 == sweeps)) {
+                const int nisw = last ? isw + 1 : isw;
+                const int f = gt < NB ? inner_rotation<T, NB>(G, tol, last ? 0 : st + 1, gt, tb.step[(gs + 1) & 1]) : 0;
+                const unsigned m = __ballot_sync(0xffffffffu, f);
+                if (gt == 0) tb.count[nisw & 1] += __popc(m);
             }
-            // J <- J R for every rotating slot
-            for (int e = gt; e < TWO * NB; e += GT) {
-                const int i = e % TWO, qs = e / TWO;
-                if (!tb.fired[qs]) continue;
-                const int p = tb.p[qs], q = tb.q[qs];
-                const R c = tb.c[qs];
-                const T es = scale(tb.ph[qs], tb.s[qs]), ces = conj_s(es);
-                const T x = J[i + p * LDG], y = J[i + q * LDG];
-                J[i + p * LDG] = add(scale(x, c), mul(y, ces));
-                J[i + q * LDG] = sub(scale(y, c), mul(x, es));
+            // the other warps: J <- J R for every rotating slot of this step
+            // (items are disjoint: all loads, then the math, then the stores)
+            if (gt >= JW0) {
+                constexpr int NJU = (TWO * NB + JWN - 1) / JWN;
+                int fj[NJU], pj[NJU], qj[NJU], ij[NJU];
+                R cj[NJU];
+                T ej[NJU], xj[NJU], yj[NJU];
+#pragma unroll
+                for (int u = 0; u < NJU; ++u) {
+                    const int e = gt - JW0 + u * JWN;
+                    fj[u] = 0;
+                    if (e >= TWO * NB) continue;
+                    const int qs = e / TWO;
+                    ij[u] = e % TWO;
+                    fj[u] = cur.fired[qs]; pj[u] = cur.p[qs]; qj[u] = cur.q[qs];
+                    cj[u] = cur.c[qs]; ej[u] = cur.es[qs];
+                }
+#pragma unroll
+                for (int u = 0; u < NJU; ++u)
+                    if (fj[u]) { xj[u] = J[ij[u] + pj[u] * LDG]; yj[u] = J[ij[u] + qj[u] * LDG]; }
+#pragma unroll
+                for (int u = 0; u < NJU; ++u)
+                    if (fj[u]) {
+                        const T es = ej[u], ces = conj_s(es);
+                        J[ij[u] + pj[u] * LDG] = add(scale(xj[u], cj[u]), mul(yj[u], ces));
+                        J[ij[u] + qj[u] * LDG] = sub(scale(yj[u], cj[u]), mul(xj[u], es));
+                    }
             }
             named_sync(bar, GT);
         }
-        const int now = *tb.count;
-        named_sync(bar, GT);   // all have read the counter before the next sweep bumps it
-        const bool quiet = (now == seen);
-        seen = now;
-        if (quiet) break;      // this sweep rotated nothing: the inner solve has converged
+        const int fired = tb.count[isw & 1];
+        named_sync(bar, GT);           // all have read it before it is reset
+        if (gt == 0) tb.count[isw & 1] = 0;   // reused by sweep isw + 2
+        seen += fired;
+        if (fired == 0) break;         // a sweep with no rotation: the inner solve has converged
     }
     return seen;
 }

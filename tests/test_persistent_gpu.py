@@ -1,0 +1,91 @@
+"""Uneven batches in one persistent launch (needs a GB300): CTAs take
+matrices of any shape from a largest-first queue and solve each whole in a
+global-memory slot.  Parity with the oracle, and agreement with the on-chip
+kernel when both use the same block width."""
+import numpy as np
+import pytest
+import torch
+
+import __graft_entry__  # noqa: F401
+import oracle
+import paper_2601_17979_gb300 as bsvd
+import synth
+from oracle import checks
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    __graft_entry__.build()
+
+
+def run_batched(mats, **kw):
+    T = [torch.from_numpy(x).cuda() for x in mats]
+    r = bsvd.gesvj_batched(T, **kw)
+    return ([s.cpu().numpy() for s in r.S], None if r.U is None else [u.cpu().numpy() for u in r.U],
+            None if r.V is None else [v.cpu().numpy() for v in r.V], r.info.cpu().numpy(), r.sweeps.cpu().numpy())
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_uneven_sample_one_launch(cplx):
+    ids = [i for i in range(80) if (i % 2 == 1) == cplx][:24]
+    mats = synth.matrices("uneven", ids)
+    S, U, V, info, sw = run_batched(mats, path="persistent")
+    ref = oracle.gesvj(mats)
+    assert (info == 0).all(), info
+    for i, A in enumerate(mats):
+        meas = checks.measures(A, S[i], U[i], V[i], ref["S"][i])
+        assert checks.violations(meas, checks.U32) == [], (i, A.shape, meas)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.complex128, np.float32])
+def test_mixed_shapes_and_edges(dtype):
+    rng = np.random.default_rng(21)
+    shapes = [(40, 24), (24, 40), (1, 1), (7, 1), (1, 7), (0, 5), (5, 0), (130, 70), (64, 64), (33, 17), (3, 3)]
+    mats = []
+    for m, n in shapes:
+        x = rng.standard_normal((m, n))
+        if np.issubdtype(dtype, np.complexfloating):
+            x = x + 1j * rng.standard_normal((m, n))
+        mats.append(x.astype(dtype))
+    mats[3][2, 0] = np.nan                                   # one non-finite matrix
+    S, U, V, info, sw = run_batched(mats, path="persistent", nb=8)
+    u = checks.unit_roundoff(dtype)
+    for i, (A, (m, n)) in enumerate(zip(mats, shapes)):
+        if min(m, n) == 0:
+            assert info[i] == 0
+            continue
+        if i == 3:
+            assert info[i] == -1 and np.isnan(S[i]).all()
+            continue
+        assert info[i] == 0
+        meas = checks.measures(A, S[i], U[i], V[i], oracle.gesvj(A)["S"])
+        assert checks.violations(meas, u) == [], (i, meas)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_persistent_agrees_with_on_chip(dtype):
+    """Same per-matrix code in both kernels; the compiler may contract
+    a*b + c*d differently in each, so they agree to the bounds, not bitwise."""
+    rng = np.random.default_rng(22)
+    shapes = [(48, 32), (32, 48), (100, 64), (20, 20)]
+    mats = [rng.standard_normal(s).astype(dtype) for s in shapes]
+    S1, U1, V1, i1, w1 = run_batched(mats, path="persistent", nb=8)
+    S2, U2, V2, i2, w2 = run_batched(mats, path="fused", nb=8)
+    u = checks.unit_roundoff(dtype)
+    assert (i1 == 0).all() and (i2 == 0).all()
+    assert np.abs(w1 - w2).max() <= 1
+    for k, A in enumerate(mats):
+        assert np.abs(S1[k] - S2[k]).max() <= 50 * min(A.shape) * u * S2[k][0]
+        meas = checks.measures(A, S1[k], U1[k], V1[k], S2[k])
+        assert checks.violations(meas, u) == [], (k, meas)
+
+
+def test_persistent_jobs_none():
+    mats = synth.matrices("uneven", range(0, 16, 2))
+    S, U, V, info, sw = run_batched(mats, path="persistent", compute_u=False, compute_v=False)
+    assert U is None and V is None and (info == 0).all()
+    ref = oracle.gesvj(mats, want_u=False, want_v=False)
+    for i in range(len(mats)):
+        assert np.abs(S[i] - ref["S"][i]).max() <= 50 * min(mats[i].shape) * checks.U32 * ref["S"][i][0]
