@@ -96,7 +96,9 @@ typedef struct {
                           bit 1: two-stage vector update (Design-3 off; multi-kernel path);
                           bit 2: no masks (Design-4 off; multi-kernel path, host-checked
                           batch convergence).  Bits 1-2 with AUTO select the multi-kernel
-                          path.                                                              */
+                          path.
+                          bit 3: no CUDA graph (the masked multi-kernel path otherwise
+                          records one sweep into a graph and replays it each sweep)    */
     int prec;          /* bsvd_prec; MIXED only for d/z and the strided form                 */
     int reserved[5];
 } bsvd_opts;
@@ -146,6 +148,28 @@ bsvd_status bsvd_sgesvj_strided(BSVD_STRIDED_ARGS(float, float));
 bsvd_status bsvd_dgesvj_strided(BSVD_STRIDED_ARGS(double, double));
 bsvd_status bsvd_cgesvj_strided(BSVD_STRIDED_ARGS(void, float));    /* T = complex float  */
 bsvd_status bsvd_zgesvj_strided(BSVD_STRIDED_ARGS(void, double));   /* T = complex double */
+
+/*
+ * Autotuner (the paper's "decision layer" of Sec. 4.2 picks a GEMM kernel from
+ * an offline table; here the whole configuration is timed online).  Times the
+ * candidates -- block width nb in {4, 8, 16, 32} x {on-chip fused path,
+ * multi-kernel path}, which also fixes the threads per matrix -- on the first
+ * min(batch, 512) matrices of the caller's strided batch (read only), keeps
+ * the fastest one whose every matrix converged, records it in the handle for
+ * the bucket (type, m and n rounded up to powers of two, jobu, jobv), and
+ * writes it to *best (base options with path and nb set).  Later AUTO calls
+ * without an explicit nb in that bucket follow it.  times_ms (8 floats, or
+ * NULL) receives each candidate's time, -1 when not run.  Synchronises
+ * `stream`.  Workspace: bsvd_autotune_workspace bytes.  Arguments:
+ *   1 handle 2 dtype 3 jobu 4 jobv 5 batch 6 m 7 n 8 dA 9 lda 10 strideA
+ *  11 d_work 12 work_bytes 13 base (NULL = defaults) 14 best 15 times_ms 16 stream
+ */
+bsvd_status bsvd_autotune_workspace(bsvd_handle handle, char dtype, int batch, int m, int n,
+                                    bsvd_job jobu, bsvd_job jobv, const bsvd_opts* base, size_t* bytes);
+bsvd_status bsvd_autotune(bsvd_handle handle, char dtype, bsvd_job jobu, bsvd_job jobv, int batch, int m,
+                          int n, const void* dA, int lda, long long strideA, void* d_work,
+                          size_t work_bytes, const bsvd_opts* base, bsvd_opts* best, float* times_ms,
+                          void* stream);
 
 /*
  * Strided FP64 batch that allocates nothing (the paper has no counterpart).

@@ -21,7 +21,8 @@ BSVD_OK = 0
 STATUS = {0: "BSVD_OK", -1: "BSVD_ERR_INVALID", -2: "BSVD_ERR_WORKSPACE", -3: "BSVD_ERR_CUDA",
           -4: "BSVD_ERR_TIMEOUT", -5: "BSVD_ERR_NOT_IMPLEMENTED", -6: "BSVD_ERR_NOMEM"}
 PATHS = {"auto": 0, "fused": 1, "plain": 2, "blocked": 3, "persistent": 4}
-FLAG_NO_V_CORRECTION, FLAG_TWO_STAGE, FLAG_NO_MASKS = 1, 2, 4
+PATH_NAMES = {v: k for k, v in PATHS.items()}
+FLAG_NO_V_CORRECTION, FLAG_TWO_STAGE, FLAG_NO_MASKS, FLAG_NO_GRAPH = 1, 2, 4, 8
 DTYPES = {torch.float32: "s", torch.float64: "d", torch.complex64: "c", torch.complex128: "z"}
 REAL = {torch.float32: torch.float32, torch.float64: torch.float64,
         torch.complex64: torch.float32, torch.complex128: torch.float64}
@@ -33,7 +34,7 @@ EXPORTS = (
     "bsvd_version", "bsvd_gesvj_workspace",
     "bsvd_sgesvj_strided", "bsvd_dgesvj_strided", "bsvd_cgesvj_strided", "bsvd_zgesvj_strided",
     "bsvd_sgesvj_batched", "bsvd_dgesvj_batched", "bsvd_cgesvj_batched", "bsvd_zgesvj_batched",
-    "bsvd_dgesvj_strided_noalloc",
+    "bsvd_dgesvj_strided_noalloc", "bsvd_autotune_workspace", "bsvd_autotune",
 )
 
 
@@ -83,6 +84,10 @@ def load() -> ctypes.CDLL:
                     ctypes.POINTER(Opts), P]
                 getattr(L, f"bsvd_{t}gesvj_batched").argtypes = [
                     P, I, I, I, P, P, P, P, P, P, P, P, P, P, P, P, SZ, ctypes.POINTER(Opts), P]
+            L.bsvd_autotune_workspace.argtypes = [P, ctypes.c_char, I, I, I, I, I, ctypes.POINTER(Opts),
+                                                  ctypes.POINTER(SZ)]
+            L.bsvd_autotune.argtypes = [P, ctypes.c_char, I, I, I, I, I, P, I, LL, P, SZ,
+                                        ctypes.POINTER(Opts), ctypes.POINTER(Opts), P, P]
             _lib = L
     return _lib
 
@@ -264,3 +269,31 @@ def gesvj_batched(mats, compute_u: bool = True, compute_v: bool = True, *, nb: i
     # keep the pointer arrays and workspace alive until the kernels finish
     torch.cuda.current_stream(dev).synchronize() if stream is None else stream.synchronize()
     return SVDResult(S, U, V, info, sweeps)
+
+
+def autotune(A: torch.Tensor, compute_u: bool = True, compute_v: bool = True, *, stream=None, **opts):
+    """Time the path x block-width candidates on (up to 512 of) A's matrices,
+    record the winner in the library handle for this (type, size bucket, jobs)
+    and return (best, times): best = {"path", "nb"}, times = {(path, nb): ms}.
+    Later gesvj calls on that bucket with path "auto" and no nb follow it."""
+    if A.dim() == 2:
+        A = A.unsqueeze(0)
+    A = column_major(A)
+    batch, m, n = A.shape
+    L, h = load(), handle()
+    t = DTYPES[A.dtype]
+    base = make_opts(**opts)
+    nbytes = ctypes.c_size_t()
+    _check(L.bsvd_autotune_workspace(h, t.encode(), batch, m, n, int(compute_u), int(compute_v),
+                                     ctypes.byref(base), ctypes.byref(nbytes)), "bsvd_autotune_workspace")
+    work = torch.empty(max(nbytes.value, 16), dtype=torch.uint8, device=A.device)
+    best = Opts()
+    times = (ctypes.c_float * 8)()
+    _check(L.bsvd_autotune(h, t.encode(), int(compute_u), int(compute_v), batch, m, n, A.data_ptr(),
+                           leading_dim(A), A.stride(0), work.data_ptr(), work.numel(), ctypes.byref(base),
+                           ctypes.byref(best), ctypes.cast(times, ctypes.c_void_p), _stream_ptr(stream)),
+           "bsvd_autotune")
+    nbs = [4, 4, 8, 8, 16, 16, 32, 32]
+    names = ["fused", "blocked"] * 4
+    tt = {(names[c], nbs[c]): times[c] for c in range(8) if times[c] >= 0}
+    return {"path": PATH_NAMES[best.path], "nb": best.nb}, tt

@@ -17,7 +17,8 @@ template <> struct BlkCfg<16> { static constexpr int GT = 128; };
 template <> struct BlkCfg<32> { static constexpr int GT = 256; };
 
 template <class T, int NB>
-cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stage, bool host_sync) {
+cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stage, bool host_sync,
+                       cudaStream_t capture) {
     using R = Real<T>;
     constexpr int TWO = 2 * NB, GT = BlkCfg<NB>::GT, LDG = TWO + 1;
     const BlkSizes z = blk_sizes(NB, a.M, a.N, two_stage);
@@ -54,39 +55,67 @@ cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stag
     blk_load<T><<<a.count, kBlkThreads, 0, st>>>(a);
     const dim3 gpair(a.count, z.L / 2);
     const dim3 gupd(a.count, z.L / 2, (a.M + a.N + kUpdRows - 1) / kUpdRows);
-    for (int sw = 0; sw < a.max_sweeps; ++sw) {
+    // one sweep: every round's stages, then the end-of-sweep bookkeeping
+    auto sweep = [&](cudaStream_t s) -> cudaError_t {
         for (int r = 0; r < z.L - 1; ++r) {
-            blk_gram<T, NB><<<gpair, kBlkThreads, 0, st>>>(a, r);
-            blk_heevj<T, NB, GT><<<gpair, GT, heevj_smem, st>>>(a, r);
+            blk_gram<T, NB><<<gpair, kBlkThreads, 0, s>>>(a, r);
+            blk_heevj<T, NB, GT><<<gpair, GT, heevj_smem, s>>>(a, r);
             if (two_stage) {
-                blk_update_stage1<T, NB><<<gupd, kUpdRows, upd_smem, st>>>(a, r);
-                blk_update_stage2<T, NB><<<gupd, kUpdRows, upd_smem, st>>>(a, r);
+                blk_update_stage1<T, NB><<<gupd, kUpdRows, upd_smem, s>>>(a, r);
+                blk_update_stage2<T, NB><<<gupd, kUpdRows, upd_smem, s>>>(a, r);
             } else {
-                blk_update_fused<T, NB><<<gupd, kUpdRows, upd_smem, st>>>(a, r);
+                blk_update_fused<T, NB><<<gupd, kUpdRows, upd_smem, s>>>(a, r);
             }
         }
-        if ((e = cudaMemsetAsync(a.any_active, 0, sizeof(int), st)) != cudaSuccess) return e;
-        blk_converge<<<(a.count + 127) / 128, 128, 0, st>>>(a);
-        if (host_sync) {
-            // batch-level convergence (the paper's unmasked design): stop once no
-            // matrix rotated in the last sweep
+        cudaError_t err = cudaMemsetAsync(a.any_active, 0, sizeof(int), s);
+        if (err != cudaSuccess) return err;
+        blk_converge<<<(a.count + 127) / 128, 128, 0, s>>>(a);
+        return cudaGetLastError();
+    };
+    if (host_sync) {
+        // batch-level convergence (the paper's unmasked design): stop once no
+        // matrix rotated in the last sweep
+        for (int sw = 0; sw < a.max_sweeps; ++sw) {
+            if ((e = sweep(st)) != cudaSuccess) return e;
             int any = 0;
             if ((e = cudaMemcpyAsync(&any, a.any_active, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
             if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
             if (!any) break;
         }
+    } else {
+        // masked: converged matrices skip every stage, so max_sweeps sweeps are
+        // issued without a host round trip; one sweep is recorded once into a
+        // CUDA graph (on the private capture stream) and replayed per sweep
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        bool graphed = false;
+        if (capture && cudaStreamBeginCapture(capture, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const cudaError_t ce = sweep(capture);
+            const cudaError_t ee = cudaStreamEndCapture(capture, &graph);
+            graphed = ce == cudaSuccess && ee == cudaSuccess && graph &&
+                      cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+            if (!graphed) cudaGetLastError();
+        }
+        for (int sw = 0; sw < a.max_sweeps; ++sw) {
+            e = graphed ? cudaGraphLaunch(exec, st) : sweep(st);
+            if (e != cudaSuccess) break;
+        }
+        if (exec) cudaGraphExecDestroy(exec);   // freed once the queued launches finish
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return e;
     }
     blk_finalize<T><<<a.count, kBlkThreads, fin_smem, st>>>(a);
     return cudaGetLastError();
 }
 
 template <class T>
-cudaError_t blk_run(int nb, const BlockedArgs& a, void* work, cudaStream_t st, bool two_stage, bool host_sync) {
+cudaError_t blk_run(int nb, const BlockedArgs& a, void* work, cudaStream_t st, bool two_stage, bool host_sync,
+                    cudaStream_t capture) {
     switch (nb) {
-        case 4: return blk_run_nb<T, 4>(a, work, st, two_stage, host_sync);
-        case 8: return blk_run_nb<T, 8>(a, work, st, two_stage, host_sync);
-        case 16: return blk_run_nb<T, 16>(a, work, st, two_stage, host_sync);
-        case 32: return blk_run_nb<T, 32>(a, work, st, two_stage, host_sync);
+        case 4: return blk_run_nb<T, 4>(a, work, st, two_stage, host_sync, capture);
+        case 8: return blk_run_nb<T, 8>(a, work, st, two_stage, host_sync, capture);
+        case 16: return blk_run_nb<T, 16>(a, work, st, two_stage, host_sync, capture);
+        case 32: return blk_run_nb<T, 32>(a, work, st, two_stage, host_sync, capture);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -95,6 +124,6 @@ cudaError_t blk_run(int nb, const BlockedArgs& a, void* work, cudaStream_t st, b
 
 #define BSVD_DEFINE_BLOCKED(TYPE, TAG)                                                          \
     cudaError_t bsvd::blocked_run_##TAG(int nb, const BlockedArgs& a, void* work, cudaStream_t st, \
-                                        bool two_stage, bool host_sync) {                       \
-        return blk_run<TYPE>(nb, a, work, st, two_stage, host_sync);                            \
+                                        bool two_stage, bool host_sync, cudaStream_t capture) { \
+        return blk_run<TYPE>(nb, a, work, st, two_stage, host_sync, capture);                   \
     }

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <map>
 #include <new>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -18,12 +19,24 @@
 #include "gesvj_fused.cuh"
 #include "internal.h"
 
+// Autotuned choice for a bucket: (type, M and N rounded up to powers of two,
+// jobu, jobv) -> path and block width.
+struct bsvd_tuned {
+    int path;
+    int nb;
+    float ms;
+};
+using bsvd_tune_key = std::tuple<char, int, int, int, int>;
+
 struct bsvd_handle_s {
     int last_arg = 0;
     int last_cuda = 0;
     int device = -1;
     int max_smem = 0;      // opt-in shared memory per block (bytes)
     int sm_count = 0;
+    std::map<bsvd_tune_key, bsvd_tuned> tuned;
+    cudaStream_t cap = nullptr;   // private stream on which sweeps are recorded into CUDA graphs
+    int cap_device = -1;
 };
 
 namespace {
@@ -60,6 +73,22 @@ bsvd_status refresh_device(bsvd_handle h) {
     return BSVD_OK;
 }
 
+// The stream on which the multi-kernel path records one sweep into a CUDA
+// graph (never the caller's: the legacy default stream cannot be captured);
+// nullptr when graphs are off (flags bit 3) or the stream cannot be made.
+cudaStream_t capture_stream(bsvd_handle h, int flags) {
+    if (flags & 8) return nullptr;
+    if (h->cap && h->cap_device == h->device) return h->cap;
+    if (h->cap) { cudaStreamDestroy(h->cap); h->cap = nullptr; }
+    if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        h->cap = nullptr;
+        return nullptr;
+    }
+    h->cap_device = h->device;
+    return h->cap;
+}
+
 struct Resolved {
     int nb, max_sweeps, inner_sweeps, path, flags, prec;
     double tol;
@@ -71,7 +100,7 @@ bool resolve(const bsvd_opts* o, bool single, int N, Resolved& r) {
     std::memset(&z, 0, sizeof z);
     if (!o) o = &z;
     if (o->nb < 0 || o->max_sweeps < 0 || o->inner_sweeps < 0 || o->tol < 0 || o->path < 0 ||
-        o->path > BSVD_PATH_PERSISTENT || o->flags < 0 || o->flags > 7 || o->prec < 0 ||
+        o->path > BSVD_PATH_PERSISTENT || o->flags < 0 || o->flags > 15 || o->prec < 0 ||
         o->prec > BSVD_PREC_MIXED || (o->prec == BSVD_PREC_MIXED && single))
         return false;
     r.nb = o->nb ? o->nb : (N >= 48 ? 16 : (N >= 12 ? 8 : 4));
@@ -85,9 +114,30 @@ bool resolve(const bsvd_opts* o, bool single, int N, Resolved& r) {
     return true;
 }
 
+int pow2_ceil(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+bsvd_tune_key tune_key(char t, int m, int n, bool wantU, bool wantV) {
+    return bsvd_tune_key(t, pow2_ceil(std::max(m, n)), pow2_ceil(std::min(m, n)), wantU ? 1 : 0, wantV ? 1 : 0);
+}
+
+// An AUTO call with no block width given follows the autotuned choice for its
+// bucket, if bsvd_autotune recorded one in this handle.
+void apply_tuned(bsvd_handle h, char t, int m, int n, bool wantU, bool wantV, const bsvd_opts* o,
+                 Resolved& r) {
+    if (!h || r.path != BSVD_PATH_AUTO || (o && o->nb) || r.prec != BSVD_PREC_NATIVE || (r.flags & 6)) return;
+    auto it = h->tuned.find(tune_key(t, m, n, wantU, wantV));
+    if (it == h->tuned.end()) return;
+    r.path = it->second.path;
+    r.nb = it->second.nb;
+}
+
 typedef size_t (*plan_fn)(int, int, int, bool, FusedArgs&, int&);
 typedef cudaError_t (*launch_fn)(int, const FusedArgs&, int, size_t, cudaStream_t);
-typedef cudaError_t (*blocked_fn)(int, const BlockedArgs&, void*, cudaStream_t, bool, bool);
+typedef cudaError_t (*blocked_fn)(int, const BlockedArgs&, void*, cudaStream_t, bool, bool, cudaStream_t);
 typedef cudaError_t (*persist_fn)(int, const bsvd::PersistArgs&, int, int, cudaStream_t);
 typedef long long (*slot_fn)(int, int, int);
 
@@ -259,7 +309,7 @@ bsvd_status mixed_impl(char t, bsvd_handle h, bool wantU, bool wantV, int batch,
         a.S = S32; a.sS = N;
         a.V = ma.V32; a.sV = (long long)N * N; a.ldv = N;
         a.info = info32; a.sweeps = sweeps32;
-        e = o32.blocked(mp.p32.nb, a, w + mp.off32, s, mp.p32.two_stage, mp.p32.host_sync);
+        e = o32.blocked(mp.p32.nb, a, w + mp.off32, s, mp.p32.two_stage, mp.p32.host_sync, capture_stream(h, r.flags));
     } else {
         FusedArgs& a = mp.p32.a;
         a.A = ma.A32; a.sA = (long long)M * N; a.lda = M;
@@ -287,7 +337,7 @@ bsvd_status mixed_impl(char t, bsvd_handle h, bool wantU, bool wantV, int batch,
         a.U = pU; a.sU = psU; a.ldu = pldu;
         a.V = pV; a.sV = psV; a.ldv = pldv;
         a.info = d_info; a.sweeps = d_sweeps;
-        e = o64.blocked(mp.p64.nb, a, w + mp.off64, s, mp.p64.two_stage, mp.p64.host_sync);
+        e = o64.blocked(mp.p64.nb, a, w + mp.off64, s, mp.p64.two_stage, mp.p64.host_sync, capture_stream(h, r.flags));
     } else {
         FusedArgs& a = mp.p64.a;
         a.A = ma.Ahat; a.sA = (long long)M * N; a.lda = M;
@@ -332,6 +382,7 @@ bsvd_status strided_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
     Resolved r;
     if (!resolve(opts, ops.single, k, r)) return fail_arg(h, 22);
     if (r.path == BSVD_PATH_PERSISTENT) r.path = BSVD_PATH_AUTO;   // one shape: the regular paths
+    apply_tuned(h, t, m, n, wantU, wantV, opts, r);
     if (batch == 0) return BSVD_OK;
     bsvd_status st = refresh_device(h);
     if (st != BSVD_OK) return st;
@@ -356,7 +407,7 @@ bsvd_status strided_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
         a.V = dV; a.sV = sV; a.ldv = ldv;
         a.info = d_info;
         a.sweeps = d_sweeps;
-        cudaError_t e = ops.blocked(p.nb, a, d_work, s, p.two_stage, p.host_sync);
+        cudaError_t e = ops.blocked(p.nb, a, d_work, s, p.two_stage, p.host_sync, capture_stream(h, r.flags));
         return e == cudaSuccess ? BSVD_OK : fail_cuda(h, e);
     }
     FusedArgs& a = p.a;
@@ -373,9 +424,9 @@ bsvd_status strided_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
 // Shape groups of a pointer-array batch, in a fixed order.
 using Groups = std::map<std::pair<int, int>, std::vector<int>>;
 
-bsvd_status plan_batched(int max_smem, const TypeOps& ops, int batch, const Groups& groups,
-                         bool wantU, bool wantV, const bsvd_opts* opts, std::vector<Plan>& plans,
-                         std::vector<Resolved>& res, size_t& total) {
+bsvd_status plan_batched(bsvd_handle h, char t, int max_smem, const TypeOps& ops, int batch,
+                         const Groups& groups, bool wantU, bool wantV, const bsvd_opts* opts,
+                         std::vector<Plan>& plans, std::vector<Resolved>& res, size_t& total) {
     total = batched_ints(batch);
     plans.assign(groups.size(), Plan());
     res.assign(groups.size(), Resolved());
@@ -383,6 +434,7 @@ bsvd_status plan_batched(int max_smem, const TypeOps& ops, int batch, const Grou
     for (auto& kv : groups) {
         const int mm = kv.first.first, nn = kv.first.second;
         if (!resolve(opts, ops.single, std::min(mm, nn), res[gi])) return BSVD_ERR_INVALID;
+        apply_tuned(h, t, mm, nn, wantU, wantV, opts, res[gi]);
         if (std::min(mm, nn) > 0) {
             bsvd_status st = plan_group(max_smem, ops, mm, nn, (int)kv.second.size(), wantU, wantV,
                                         res[gi], plans[gi]);
@@ -533,8 +585,8 @@ bsvd_status batched_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
     std::vector<Plan> plans;
     std::vector<Resolved> res;
     size_t need = 0;
-    bsvd_status st = plan_batched(device_smem_or_default(h), ops, batch, groups, wantU, wantV, opts,
-                                  plans, res, need);
+    bsvd_status st = plan_batched(h, t, device_smem_or_default(h), ops, batch, groups, wantU, wantV,
+                                  opts, plans, res, need);
     if (st == BSVD_ERR_INVALID) return fail_arg(h, 18);
     if (st != BSVD_OK) return st;
     if (!d_work || work_bytes < need) return BSVD_ERR_WORKSPACE;
@@ -584,7 +636,7 @@ bsvd_status batched_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
             a.index = index;
             a.info = d_info;
             a.sweeps = d_sweeps;
-            e = ops.blocked(p.nb, a, region, s, p.two_stage, p.host_sync);
+            e = ops.blocked(p.nb, a, region, s, p.two_stage, p.host_sync, capture_stream(h, r.flags));
             region += align256(p.bytes);
         } else {
             FusedArgs& a = p.a;
@@ -608,6 +660,61 @@ size_t bsvd::blocked_bytes(int nb, int M, int N, int count, bool two_stage, size
     return blk_bytes(nb, M, N, count, two_stage, elt);
 }
 
+namespace {
+
+// Candidates of the autotuner: block width x {on-chip fused, multi-kernel}.
+// The block width also sets the threads per matrix (64, 128 or 256 per CTA
+// on chip; 128-thread update CTAs and 32-256-thread eigensolver CTAs on the
+// multi-kernel path).
+constexpr int kTuneCands = 8;
+constexpr int kTuneBatch = 512;
+void tune_cand(int c, int& path, int& nb) {
+    static const int nbs[4] = {4, 8, 16, 32};
+    nb = nbs[c / 2];
+    path = (c % 2 == 0) ? BSVD_PATH_FUSED : BSVD_PATH_BLOCKED;
+}
+
+struct TuneLayout {
+    size_t off[5];      // S, U, V, info, sweeps
+    size_t cand_off;    // candidate workspace
+    size_t bytes;
+};
+
+bsvd_status tune_layout(bsvd_handle h, char t, int tb, int m, int n, bool wantU, bool wantV,
+                        const bsvd_opts* base, TuneLayout& L, bool feasible[kTuneCands]) {
+    const TypeOps ops = ops_for(t);
+    const int k = std::min(m, n);
+    const size_t rsz = ops.single ? 4 : 8;
+    const size_t sizes[5] = {(size_t)tb * k * rsz, wantU ? (size_t)tb * m * k * ops.elt : 0,
+                             wantV ? (size_t)tb * n * k * ops.elt : 0, (size_t)tb * sizeof(int),
+                             (size_t)tb * sizeof(int)};
+    size_t pos = 0;
+    for (int i = 0; i < 5; ++i) { L.off[i] = pos; pos += align256(sizes[i]); }
+    L.cand_off = pos;
+    size_t need = 0;
+    const int max_smem = device_smem_or_default(h);
+    for (int c = 0; c < kTuneCands; ++c) {
+        bsvd_opts o;
+        if (base) o = *base;
+        else std::memset(&o, 0, sizeof o);
+        tune_cand(c, o.path, o.nb);
+        o.prec = BSVD_PREC_NATIVE;
+        o.flags &= 1;
+        feasible[c] = false;
+        Resolved r;
+        if (!resolve(&o, ops.single, k, r)) continue;
+        if (r.nb > std::max(4, 2 * k)) continue;            // wider than the matrix: pointless
+        Plan p;
+        if (plan_group(max_smem, ops, m, n, tb, wantU, wantV, r, p) != BSVD_OK) continue;
+        feasible[c] = true;
+        if (p.blocked) need = std::max(need, p.bytes);
+    }
+    L.bytes = pos + align256(need);
+    return BSVD_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 bsvd_status bsvd_create(bsvd_handle* handle) {
@@ -617,6 +724,7 @@ bsvd_status bsvd_create(bsvd_handle* handle) {
 }
 
 bsvd_status bsvd_destroy(bsvd_handle handle) {
+    if (handle && handle->cap) cudaStreamDestroy(handle->cap);
     delete handle;
     return BSVD_OK;
 }
@@ -660,6 +768,7 @@ bsvd_status bsvd_gesvj_workspace(bsvd_handle handle, char dtype, int batch, cons
         Resolved r;
         if (!resolve(opts, ops.single, std::min(m, n), r)) return fail_arg(handle, 9);
         if (r.path == BSVD_PATH_PERSISTENT) r.path = BSVD_PATH_AUTO;   // as the strided call does
+        apply_tuned(handle, dtype, m, n, wantU, wantV, opts, r);
         if (r.prec == BSVD_PREC_MIXED) {
             MixedPlan mp;
             bsvd_status st = plan_mixed(max_smem, dtype, m, n, batch, wantU, wantV, r, mp);
@@ -687,9 +796,103 @@ bsvd_status bsvd_gesvj_workspace(bsvd_handle handle, char dtype, int batch, cons
     }
     std::vector<Plan> plans;
     std::vector<Resolved> res;
-    bsvd_status st = plan_batched(max_smem, ops, batch, groups, wantU, wantV, opts, plans, res, *bytes);
+    bsvd_status st = plan_batched(handle, dtype, max_smem, ops, batch, groups, wantU, wantV, opts, plans,
+                                  res, *bytes);
     if (st == BSVD_ERR_INVALID) return fail_arg(handle, 9);
     return st;
+}
+
+bsvd_status bsvd_autotune_workspace(bsvd_handle handle, char dtype, int batch, int m, int n,
+                                    bsvd_job jobu, bsvd_job jobv, const bsvd_opts* base, size_t* bytes) {
+    if (!handle) return BSVD_ERR_INVALID;
+    handle->last_arg = 0;
+    if (dtype != 's' && dtype != 'd' && dtype != 'c' && dtype != 'z') return fail_arg(handle, 2);
+    if (batch < 1) return fail_arg(handle, 3);
+    if (m < 1) return fail_arg(handle, 4);
+    if (n < 1) return fail_arg(handle, 5);
+    if (!bytes) return fail_arg(handle, 9);
+    TuneLayout L;
+    bool feas[kTuneCands];
+    tune_layout(handle, dtype, std::min(batch, kTuneBatch), m, n, jobu == BSVD_JOB_SOME, jobv == BSVD_JOB_SOME,
+                base, L, feas);
+    *bytes = L.bytes;
+    return BSVD_OK;
+}
+
+bsvd_status bsvd_autotune(bsvd_handle handle, char dtype, bsvd_job jobu, bsvd_job jobv, int batch, int m,
+                          int n, const void* dA, int lda, long long strideA, void* d_work,
+                          size_t work_bytes, const bsvd_opts* base, bsvd_opts* best, float* times_ms,
+                          void* stream) {
+    if (!handle) return BSVD_ERR_INVALID;
+    handle->last_arg = 0;
+    if (dtype != 's' && dtype != 'd' && dtype != 'c' && dtype != 'z') return fail_arg(handle, 2);
+    if (jobu != BSVD_JOB_NONE && jobu != BSVD_JOB_SOME) return fail_arg(handle, 3);
+    if (jobv != BSVD_JOB_NONE && jobv != BSVD_JOB_SOME) return fail_arg(handle, 4);
+    if (batch < 1) return fail_arg(handle, 5);
+    if (m < 1) return fail_arg(handle, 6);
+    if (n < 1) return fail_arg(handle, 7);
+    if (!dA) return fail_arg(handle, 8);
+    if (lda < m) return fail_arg(handle, 9);
+    if (batch > 1 && strideA < (long long)lda * n) return fail_arg(handle, 10);
+    if (!best) return fail_arg(handle, 14);
+    const bool wantU = jobu == BSVD_JOB_SOME, wantV = jobv == BSVD_JOB_SOME;
+    const int tb = std::min(batch, kTuneBatch), k = std::min(m, n);
+    bsvd_status st = refresh_device(handle);
+    if (st != BSVD_OK) return st;
+    TuneLayout L;
+    bool feas[kTuneCands];
+    tune_layout(handle, dtype, tb, m, n, wantU, wantV, base, L, feas);
+    if (!d_work || work_bytes < L.bytes) return BSVD_ERR_WORKSPACE;
+    char* w = static_cast<char*>(d_work);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return fail_cuda(handle, cudaGetLastError());
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail_cuda(handle, cudaGetLastError()); }
+    std::vector<int> info(tb);
+    int best_c = -1;
+    float best_ms = 0.f;
+    for (int c = 0; c < kTuneCands; ++c) {
+        if (times_ms) times_ms[c] = -1.f;
+        if (!feas[c]) continue;
+        bsvd_opts o;
+        if (base) o = *base;
+        else std::memset(&o, 0, sizeof o);
+        tune_cand(c, o.path, o.nb);
+        o.prec = BSVD_PREC_NATIVE;
+        o.flags &= 1;
+        float ms = 0.f;
+        bool ok = true;
+        for (int rep = 0; rep < 2 && ok; ++rep) {      // the first run warms up, the second is timed
+            cudaEventRecord(e0, s);
+            st = strided_impl(dtype, handle, jobu, jobv, tb, m, n, dA, lda, strideA, w + L.off[0], k,
+                              w + L.off[1], m, (long long)m * k, w + L.off[2], n, (long long)n * k,
+                              reinterpret_cast<int*>(w + L.off[3]), reinterpret_cast<int*>(w + L.off[4]),
+                              w + L.cand_off, L.bytes - L.cand_off, &o, stream);
+            cudaEventRecord(e1, s);
+            if (st != BSVD_OK || cudaEventSynchronize(e1) != cudaSuccess) { ok = false; break; }
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (!ok) { cudaGetLastError(); continue; }
+        if (cudaMemcpy(info.data(), w + L.off[3], sizeof(int) * tb, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        bool conv = true;                                    // every matrix must converge
+        for (int v : info) conv = conv && v == 0;
+        if (!conv) continue;
+        if (times_ms) times_ms[c] = ms;
+        if (best_c < 0 || ms < best_ms) { best_c = c; best_ms = ms; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (best_c < 0) return BSVD_ERR_NOT_IMPLEMENTED;
+    bsvd_opts o;
+    if (base) o = *base;
+    else std::memset(&o, 0, sizeof o);
+    tune_cand(best_c, o.path, o.nb);
+    *best = o;
+    handle->tuned[tune_key(dtype, m, n, wantU, wantV)] = bsvd_tuned{o.path, o.nb, best_ms};
+    return BSVD_OK;
 }
 
 #define BSVD_STRIDED_IMPL(TAG, T, R)                                                          \

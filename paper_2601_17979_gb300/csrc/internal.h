@@ -41,7 +41,7 @@ size_t blocked_bytes(int nb, int M, int N, int count, bool two_stage, size_t elt
 
 #define BSVD_DECLARE_BLOCKED(TAG)                                                               \
     cudaError_t blocked_run_##TAG(int nb, const BlockedArgs& a, void* work, cudaStream_t st,   \
-                                  bool two_stage, bool host_sync);
+                                  bool two_stage, bool host_sync, cudaStream_t capture);
 
 BSVD_DECLARE_BLOCKED(s)
 BSVD_DECLARE_BLOCKED(d)

@@ -60,6 +60,7 @@ extern "C" bsvd_status bsvd_dgesvj_strided_noalloc(
     if (opts) o = *opts;
     else std::memset(&o, 0, sizeof o);
     if (o.path != BSVD_PATH_PLAIN) o.path = BSVD_PATH_BLOCKED;
+    o.flags |= 8;   // no CUDA graph: instantiating one may allocate device memory
     void* scratch = nullptr;
     if (batch > 0 && m > 0 && n > 0) {
         const bsvd_status st = static_scratch(&scratch);
