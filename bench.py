@@ -296,6 +296,177 @@ def run_uneven(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def serve_stream(srv, rate, seconds, drain, stream, pool_cache):
+    """Replay one Poisson stream at the server; collect until drained or until
+    `drain` seconds after the last arrival.  Returns the per-request records
+    of completed requests and the server counters."""
+    tr = synth.serving_trace(rate, seconds, stream=stream)
+    keys = list(zip(tr["bin"].tolist(), tr["tall"].tolist(), tr["dtype"].tolist(), tr["variant"].tolist()))
+    for k in set(keys):
+        if k not in pool_cache:
+            import torch
+            A = synth.serving_matrix(*k)
+            pool_cache[k] = torch.from_numpy(np.ascontiguousarray(A.T)).pin_memory().t()
+    mats = [pool_cache[k] for k in keys]
+    got, stop = [], threading.Event()
+
+    def collector():
+        while not stop.is_set():
+            got.append(srv.collect(1 << 16))
+            time.sleep(0.005)
+        got.append(srv.collect(1 << 20))
+
+    before = srv.stats()
+    th = threading.Thread(target=collector, daemon=True)
+    th.start()
+    ids, t0 = srv.replay(tr["t"], mats, keep=False)
+    t_arrivals = srv.clock()
+    at_end = srv.stats()
+    while srv.clock() < t_arrivals + drain:
+        st = srv.stats()
+        if st["queued"] == 0 and st["running"] == 0:
+            break
+        time.sleep(0.01)
+    t_stop = srv.clock()
+    final = srv.stats()
+    # what is left is cancelled (running persistent batches stop taking matrices)
+    srv.cancel()
+    t_cancel = time.monotonic()
+    while srv.stats()["running_batches"] > 0 and time.monotonic() < t_cancel + 300:
+        time.sleep(0.01)
+    stop.set()
+    th.join()
+    rec = {k: np.concatenate([g[k] for g in got]) if got else np.zeros(0) for k in
+           ("id", "status", "info", "sweeps", "t_submit", "t_done")}
+    mine = (rec["id"] >= ids[0]) & (rec["id"] <= ids[-1])
+    rec = {k: v[mine] for k, v in rec.items()}
+    idx = rec["id"] - ids[0]
+    return tr, ids, t0, t_arrivals, t_stop, rec, idx, before, at_end, final
+
+
+def summarize_stream(tr, ids, t0, t_arrivals, t_stop, rec, idx, before, at_end, final, seconds):
+    ok = rec["status"] == 0
+    lat = (rec["t_done"] - rec["t_submit"])[ok] * 1e3
+    n_sub = len(ids)
+    n_done = int(ok.sum())
+    sizes = synth.serving_sizes()
+    m = sizes[tr["bin"][idx[ok]]]
+    n = np.where(tr["tall"][idx[ok]], -(-m // 2), m)
+    cplx = tr["dtype"][idx[ok]] == "c"
+    sw = rec["sweeps"][ok]
+    flops = 0.0
+    for mm, nn, c, k in zip(m.tolist(), n.tolist(), cplx.tolist(), sw.tolist()):
+        f = matrix_flops(mm, nn, 16 if nn >= 48 else (8 if nn >= 12 else 4), [k])
+        flops += 4 * f if c else f
+    span = max(float(rec["t_done"][ok].max()) - t0, 1e-9) if n_done else 1e-9
+    in_window = int((rec["t_done"][ok] <= t_arrivals).sum())
+    pct = (lambda q: float(np.percentile(lat, q)) if n_done else None)
+    backlog = (at_end["queued"] + at_end["running"]) - (before["queued"] + before["running"])
+    out = {"submitted": int(n_sub), "completed": n_done, "cancelled": int((rec["status"] == -7).sum()),
+           "failed": int(((rec["status"] != 0) & (rec["status"] != -7)).sum()),
+           "completed_by_end_of_arrivals": in_window,
+           "throughput_rps": n_done / span, "throughput_in_window_rps": in_window / seconds,
+           "gflops": flops / span / 1e9,
+           "latency_ms": {"p50": pct(50), "p99": pct(99), "max": float(lat.max()) if n_done else None},
+           "backlog_at_end_of_arrivals": int(backlog),
+           "drained": bool(final["queued"] == 0 and final["running"] == 0),
+           "drain_s": t_stop - t_arrivals, "info_nonzero": int((rec["info"][ok] != 0).sum()),
+           "arena_peak_gb": final["arena_peak"] / 1e9}
+    if not out["drained"] and out["throughput_rps"] > 0:
+        out["left_at_stop"] = int(final["queued"] + final["running"])
+        out["drain_estimate_s"] = out["left_at_stop"] / out["throughput_rps"]
+    return out
+
+
+def run_serving(args, rank, world, local):
+    """Serving stream: Poisson arrivals replayed at the continuous-batching
+    server; throughput, p50/p99 latency, backlog, and a rate sweep."""
+    import torch
+    import paper_2601_17979_gb300 as bsvd
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    bsvd.build()
+    cfg = synth.SERVING
+    rate = args.rate or cfg["rate"]
+    seconds = args.seconds or cfg["seconds"]
+    pool = {}
+    srv = bsvd.Server(int(args.arena_gb * 1e9), max_inflight=32)
+    # warm-up: a short low-rate stream (first launches set kernel attributes)
+    for _ in range(max(1, args.warmup)):
+        serve_stream(srv, 500.0, 0.2, 30.0, 1000 + rank, pool)
+    if dist is not None:
+        dist.barrier()
+    sampler = ClockSampler(gpu_uuid(torch, dev))
+    with sampler:
+        r = serve_stream(srv, rate, seconds, args.drain, rank, pool)
+    main = summarize_stream(*r, seconds)
+    sweep = []
+    for k, lam in enumerate(args.sweep_rates):
+        rr = serve_stream(srv, lam, args.sweep_seconds, args.sweep_seconds, 100 + 10 * k + rank, pool)
+        s_ = summarize_stream(*rr, args.sweep_seconds)
+        sweep.append({"rate_rps": lam, "p50_ms": s_["latency_ms"]["p50"], "p99_ms": s_["latency_ms"]["p99"],
+                      "throughput_rps": s_["throughput_rps"], "completed": s_["completed"],
+                      "submitted": s_["submitted"], "drained": s_["drained"]})
+    batches = srv.stats()["batches"]
+    srv.close()
+    value = main["throughput_rps"]
+    if dist is not None:
+        t = torch.tensor([value], device=dev, dtype=torch.float64)
+        dist.all_reduce(t)
+        value = float(t.item())
+    sustained = [x["rate_rps"] for x in sweep if x["drained"] and x["completed"] == x["submitted"]]
+    line = {"metric": "serving throughput (Poisson stream) with p50/p99 latency", "value": value,
+            "unit": "requests/s", "n_gpus": world, "steps": 1, "warmup": args.warmup,
+            "ms_per_step": seconds * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64+c64", "data": "synthetic",
+            "config": {"workload": f"serving: Poisson arrivals {rate:g}/s for {seconds:g} s, m log-uniform "
+                                   "16..1024 (64 log-spaced bins), half square, half 2:1 tall, 50% FP32 / "
+                                   "30% FP64 / 20% complex64, kappa log-uniform 1e2..1e6, logrand sigma, "
+                                   "Haar factors; inputs from a pool of 2 matrices per (bin, shape, type)",
+                       "arena_gb": args.arena_gb, "max_inflight": 32, "jobs": "U, Sigma, V",
+                       "results": "left in the arena and released on completion (not copied back)",
+                       "l2": "inputs read once from page-locked host memory"},
+            "latency_ms": main["latency_ms"], "serving": main, "rate_sweep": sweep,
+            "highest_sustained_rate_rps": max(sustained) if sustained else None,
+            "gpu_launches": batches, "clocks": sampler.summary()}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = serving_cpu_baseline(r[0])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def serving_cpu_baseline(tr, small=300, large=8):
+    """The oracle on a bounded sample of the stream: the first `small`
+    requests with m <= 256 and the first `large` above, timed per stratum
+    (OpenMP over matrices), combined by the stream's mix into requests/s."""
+    import oracle
+    O = oracle.default()
+    sizes = synth.serving_sizes()
+    m_all = sizes[tr["bin"]]
+    out = {}
+    tot = 0.0
+    for name, sel, cnt in (("small", m_all <= 256, small), ("large", m_all > 256, large)):
+        idx = np.flatnonzero(sel)[:cnt]
+        mats = [synth.serving_matrix(int(tr["bin"][i]), bool(tr["tall"][i]), str(tr["dtype"][i]),
+                                     int(tr["variant"][i])) for i in idx]
+        t0 = time.perf_counter()
+        res = O.gesvj(mats)
+        dt = time.perf_counter() - t0
+        out[name] = (len(mats), dt, res["threads"])
+        tot += sel.mean() * dt / max(len(mats), 1)
+    cores = out["small"][2]
+    return {"value": 1.0 / tot, "unit": "requests/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {out['small'][0]} requests with m <= 256 ({out['small'][1]:.1f} s) and first "
+                      f"{out['large'][0]} with m > 256 ({out['large'][1]:.1f} s) of the stream, Alg. 2 in FP64, "
+                      "OpenMP over matrices, weighted by the stream's mix"}
+
+
 def config_dict(world, per_rank):
     return {"workload": "tall128x64: 10,000 FP64 (sigma geometric 1..1e-6) + 10,000 FP32 "
                         "(1..1e-3) matrices 128x64 = Q1 diag(sigma) Q2^T, Haar Q1, Q2",
@@ -317,9 +488,16 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 baseline path")
     ap.add_argument("--ladder", action="store_true", help="also time Design-2/3/4 (multi-kernel)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision FP64 leg")
-    ap.add_argument("--workload", default="tall128x64", choices=["tall128x64", "uneven"],
-                    help="tall128x64 (default) or uneven: 10,000 FP32 + 10,000 complex64 matrices, "
-                         "m ~ U{8..512}, n ~ U{8..m}, one persistent launch per type")
+    ap.add_argument("--workload", default="tall128x64", choices=["tall128x64", "uneven", "serving"],
+                    help="tall128x64 (default); uneven: 10,000 FP32 + 10,000 complex64 matrices, "
+                         "m ~ U{8..512}, n ~ U{8..m}, one persistent launch per type; serving: a Poisson "
+                         "stream of single-matrix requests at the continuous-batching server")
+    ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (default 50,000)")
+    ap.add_argument("--seconds", type=float, default=0.0, help="serving: stream length (default 10 s)")
+    ap.add_argument("--drain", type=float, default=10.0, help="serving: seconds to drain after arrivals")
+    ap.add_argument("--arena-gb", type=float, default=40.0, help="serving: device-memory budget")
+    ap.add_argument("--sweep-rates", type=float, nargs="*", default=[25, 50, 100, 200])
+    ap.add_argument("--sweep-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
 
@@ -332,6 +510,9 @@ def main():
         return
     if args.workload == "uneven":
         run_uneven(args, rank, world, local)
+        return
+    if args.workload == "serving":
+        run_serving(args, rank, world, local)
         return
 
     import torch

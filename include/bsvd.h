@@ -55,7 +55,8 @@ typedef enum {
     BSVD_ERR_CUDA = -3,             /* a CUDA call failed; see bsvd_last_cuda() */
     BSVD_ERR_TIMEOUT = -4,          /* a bounded device wait expired            */
     BSVD_ERR_NOT_IMPLEMENTED = -5,  /* shape/type/option combination not built  */
-    BSVD_ERR_NOMEM = -6             /* host allocation failed                   */
+    BSVD_ERR_NOMEM = -6,            /* host allocation failed                   */
+    BSVD_ERR_CANCELLED = -7         /* a server request cancelled before it ran */
 } bsvd_status;
 
 typedef enum { BSVD_JOB_NONE = 0, BSVD_JOB_SOME = 1 } bsvd_job;   /* economy-size vectors */
@@ -212,6 +213,135 @@ bsvd_status bsvd_sgesvj_batched(BSVD_BATCHED_ARGS(float, float));
 bsvd_status bsvd_dgesvj_batched(BSVD_BATCHED_ARGS(double, double));
 bsvd_status bsvd_cgesvj_batched(BSVD_BATCHED_ARGS(void, float));
 bsvd_status bsvd_zgesvj_batched(BSVD_BATCHED_ARGS(void, double));
+
+/*
+ * Serving loop: a stream of single-matrix requests, solved with continuous
+ * batching.  The paper solves whole batches given at once and has no
+ * serving layer; this one is built on the persistent launch above (Sec. 7's
+ * per-matrix masking carried to its end: a matrix that converges leaves its
+ * CTA, which takes the next matrix of the batch).
+ *
+ * A worker thread owned by the server takes queued requests in arrival
+ * order, groups them into batches of one key (type, jobs, block width 4/8/16
+ * from min(m, n) as the AUTO choice; above big_k columns also the shape),
+ * and launches each batch on a stream of its own, up to max_inflight batches
+ * at once: requests that arrive while batches run start as soon as a stream
+ * and device memory are free, and new batches take over SMs as the CTAs of
+ * earlier ones run out of matrices.  Requests with min(m, n) <= big_k run in
+ * the persistent kernel (one CTA per matrix, its A, V and sweep state
+ * resident until it converges), and each one completes the moment its CTA
+ * raises its flag in host-mapped memory, without waiting for the rest of its
+ * batch.  Larger requests run on the multi-kernel path (many CTAs per
+ * matrix) and complete with their batch.  A request's arithmetic does not
+ * depend on what it is batched with, so its result is the same, bit for
+ * bit, alone or in any mix.
+ *
+ * Memory: every device byte the server uses comes from the caller's arena
+ * (d_arena, arena_bytes; 256-byte aligned, owned by the caller, not freed):
+ * per batch its workspace (freed when the batch ends) and its requests'
+ * outputs S, U, V (freed when the last of them is released).  A batch is
+ * admitted only if both fit; otherwise the queue waits (first come, first
+ * served) until memory is released.  A request that could not fit even in
+ * an empty arena completes at once with status BSVD_ERR_WORKSPACE.
+ * Unreleased results hold their memory: release them.
+ *
+ * Inputs are read in place by the kernels: A must be device memory or
+ * page-locked host memory (cudaHostAlloc / cudaHostRegister), checked at
+ * submit (pageable memory returns BSVD_ERR_INVALID), and must stay valid and
+ * unchanged until the request completes.
+ *
+ * Times are seconds of the steady clock bsvd_server_clock() reads; a
+ * request's latency is t_done - t_submit, t_done the moment the worker saw
+ * its completion.
+ */
+typedef struct bsvd_server_s* bsvd_server;
+
+typedef struct {
+    int max_inflight;   /* batches on the GPU at once, each on its own stream; 0 = 32, at most 64;
+                           multi-kernel batches hold at most max_inflight - max(2, max_inflight/4) */
+    int max_batch;      /* requests per persistent batch; 0 = 4096                               */
+    int big_k;          /* min(m, n) above which the multi-kernel path serves; 0 = 256          */
+    int max_big_batch;  /* requests per multi-kernel batch; 0 = 64                               */
+    int reserved[4];    /* zero                                                                  */
+} bsvd_server_opts;
+
+double bsvd_server_clock(void);
+
+/* Creates a server on the current device (opts NULL = defaults).
+ * BSVD_ERR_INVALID: null out, arena NULL, misaligned or under 1 MiB, bad opts. */
+bsvd_status bsvd_server_create(void* d_arena, size_t arena_bytes, const bsvd_server_opts* opts,
+                               bsvd_server* out);
+
+/* Queues the SVD of one m x n matrix (column-major, leading dimension lda) of
+ * type dtype ('s', 'd', 'c', 'z'); jobu / jobv as for the batch calls.  Returns
+ * a request id (> 0) in *id.  Thread-safe. */
+bsvd_status bsvd_server_submit(bsvd_server server, char dtype, int m, int n, const void* A, int lda,
+                               bsvd_job jobu, bsvd_job jobv, long long* id);
+
+/* Submits `count` requests, request i at t0 + t_offset[i] (t0 = the clock at
+ * the call, t_offset ascending, seconds), each with that scheduled time as
+ * its t_submit: a load generator that replays an arrival trace at the
+ * server, returning once the last request is queued.  ids (count) receives
+ * the ids, *t0 the start time.  Stops at the first request submit rejects
+ * and returns its status (ids of the ones before are valid). */
+bsvd_status bsvd_server_replay(bsvd_server server, int count, const double* t_offset, const char* dtype,
+                               const int* m, const int* n, const void* const* A, const int* lda,
+                               bsvd_job jobu, bsvd_job jobv, long long* ids, double* t0);
+
+/* 1: done (results ready), 0: queued or running, BSVD_ERR_WORKSPACE: the
+ * request can never fit the arena, BSVD_ERR_CUDA: its batch failed to launch
+ * or run, BSVD_ERR_CANCELLED: cancelled, BSVD_ERR_INVALID: unknown or
+ * released id. */
+int bsvd_server_test(bsvd_server server, long long id);
+
+/* Blocks until the request completes or timeout_s passes (< 0: no limit;
+ * BSVD_ERR_TIMEOUT then).  info: as d_info of the batch calls; sweeps; t_done.
+ * Any output pointer may be NULL.  Returns the request's status (see test). */
+bsvd_status bsvd_server_wait(bsvd_server server, long long id, double timeout_s, int* info, int* sweeps,
+                             double* t_done);
+
+/* Device pointers to a done request's S (k reals), U (m x k, ld *ldu) and
+ * V (n x k, ld *ldv) in the arena, valid until it is released (NULL when
+ * not computed). */
+bsvd_status bsvd_server_result(bsvd_server server, long long id, void** dS, void** dU, int* ldu,
+                               void** dV, int* ldv);
+
+/* Copies a done request's S, U (ldu >= m), V (ldv >= n) into caller memory
+ * (host or device; NULL skips), synchronously.  Do not release the request
+ * while a fetch of it runs. */
+bsvd_status bsvd_server_fetch(bsvd_server server, long long id, void* S, void* U, int ldu, void* V,
+                              int ldv);
+
+/* Frees a completed request's outputs and forgets it.  BSVD_ERR_INVALID if
+ * it is unknown or not complete. */
+bsvd_status bsvd_server_release(bsvd_server server, long long id);
+
+/* Completion queue: writes up to max requests completed since the last
+ * collect (in completion order) and returns how many; with release != 0 they
+ * are released as they are collected.  status: 0 or the failure status;
+ * info, sweeps as for wait; any array may be NULL. */
+int bsvd_server_collect(bsvd_server server, int max, int release, long long* ids, int* status, int* info,
+                        int* sweeps, double* t_submit, double* t_done);
+
+/* Cancels every queued request and stops the running persistent batches
+ * from starting more matrices (those already started finish; multi-kernel
+ * batches run to their end).  Each request that does not run completes with
+ * status BSVD_ERR_CANCELLED.  Returns at once. */
+bsvd_status bsvd_server_cancel(bsvd_server server);
+
+/* paused != 0: admit no new batch (queued requests wait, running batches
+ * go on); 0: resume.  For draining a server or forming one batch on purpose. */
+bsvd_status bsvd_server_pause(bsvd_server server, int paused);
+
+/* counters[10]: submitted, completed, failed, queued, running requests,
+ * running batches, arena bytes in use, peak arena bytes in use, cancelled,
+ * batches launched. */
+bsvd_status bsvd_server_stats(bsvd_server server, long long* counters);
+
+/* Cancels as bsvd_server_cancel does, waits for the running batches to end,
+ * frees everything the server owns (not the arena).  Not concurrent with
+ * other calls on the server. */
+bsvd_status bsvd_server_destroy(bsvd_server server);
 
 #ifdef __cplusplus
 }

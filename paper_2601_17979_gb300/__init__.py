@@ -11,10 +11,10 @@ masking, as hand-written CUDA kernels behind the C-ABI of include/bsvd.h.
     res.S, res.U, res.V, res.info, res.sweeps
 """
 from .buildlib import build
-from .binding import (BsvdError, SVDResult, gesvj, gesvj_batched, autotune, load, handle, make_opts,
+from .binding import (BsvdError, SVDResult, Server, gesvj, gesvj_batched, autotune, load, handle, make_opts,
                       column_major, empty_column_major, workspace_bytes, EXPORTS,
                       FLAG_NO_V_CORRECTION, FLAG_TWO_STAGE, FLAG_NO_MASKS, FLAG_NO_GRAPH)
 
-__all__ = ["build", "BsvdError", "SVDResult", "gesvj", "gesvj_batched", "autotune", "load", "handle",
+__all__ = ["build", "BsvdError", "SVDResult", "Server", "gesvj", "gesvj_batched", "autotune", "load", "handle",
            "make_opts", "column_major", "empty_column_major", "workspace_bytes", "EXPORTS",
            "FLAG_NO_V_CORRECTION", "FLAG_TWO_STAGE", "FLAG_NO_MASKS", "FLAG_NO_GRAPH"]

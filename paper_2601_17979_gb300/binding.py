@@ -19,7 +19,8 @@ from . import buildlib as _build
 
 BSVD_OK = 0
 STATUS = {0: "BSVD_OK", -1: "BSVD_ERR_INVALID", -2: "BSVD_ERR_WORKSPACE", -3: "BSVD_ERR_CUDA",
-          -4: "BSVD_ERR_TIMEOUT", -5: "BSVD_ERR_NOT_IMPLEMENTED", -6: "BSVD_ERR_NOMEM"}
+          -4: "BSVD_ERR_TIMEOUT", -5: "BSVD_ERR_NOT_IMPLEMENTED", -6: "BSVD_ERR_NOMEM",
+          -7: "BSVD_ERR_CANCELLED"}
 PATHS = {"auto": 0, "fused": 1, "plain": 2, "blocked": 3, "persistent": 4}
 PATH_NAMES = {v: k for k, v in PATHS.items()}
 FLAG_NO_V_CORRECTION, FLAG_TWO_STAGE, FLAG_NO_MASKS, FLAG_NO_GRAPH = 1, 2, 4, 8
@@ -35,6 +36,11 @@ EXPORTS = (
     "bsvd_sgesvj_strided", "bsvd_dgesvj_strided", "bsvd_cgesvj_strided", "bsvd_zgesvj_strided",
     "bsvd_sgesvj_batched", "bsvd_dgesvj_batched", "bsvd_cgesvj_batched", "bsvd_zgesvj_batched",
     "bsvd_dgesvj_strided_noalloc", "bsvd_autotune_workspace", "bsvd_autotune",
+    "bsvd_server_clock", "bsvd_server_create", "bsvd_server_submit", "bsvd_server_replay",
+    "bsvd_server_test", "bsvd_server_wait", "bsvd_server_result", "bsvd_server_fetch",
+    "bsvd_server_release", "bsvd_server_collect", "bsvd_server_cancel", "bsvd_server_pause",
+    "bsvd_server_stats",
+    "bsvd_server_destroy",
 )
 
 
@@ -44,6 +50,11 @@ class BsvdError(RuntimeError):
         extra = f" (argument {arg})" if arg else ""
         extra += f" (cudaError {cuda})" if status == -3 else ""
         super().__init__(f"{where}: {STATUS.get(status, status)}{extra}")
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("max_inflight", ctypes.c_int), ("max_batch", ctypes.c_int), ("big_k", ctypes.c_int),
+                ("max_big_batch", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class Opts(ctypes.Structure):
@@ -88,6 +99,22 @@ def load() -> ctypes.CDLL:
                                                   ctypes.POINTER(SZ)]
             L.bsvd_autotune.argtypes = [P, ctypes.c_char, I, I, I, I, I, P, I, LL, P, SZ,
                                         ctypes.POINTER(Opts), ctypes.POINTER(Opts), P, P]
+            D = ctypes.c_double
+            L.bsvd_server_clock.restype = D
+            L.bsvd_server_create.argtypes = [P, SZ, ctypes.POINTER(ServerOpts), ctypes.POINTER(P)]
+            L.bsvd_server_submit.argtypes = [P, ctypes.c_char, I, I, P, I, I, I, ctypes.POINTER(LL)]
+            L.bsvd_server_replay.argtypes = [P, I, P, P, P, P, P, P, I, I, P, ctypes.POINTER(D)]
+            L.bsvd_server_test.argtypes = [P, LL]
+            L.bsvd_server_wait.argtypes = [P, LL, D, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]
+            L.bsvd_server_result.argtypes = [P, LL, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(I),
+                                             ctypes.POINTER(P), ctypes.POINTER(I)]
+            L.bsvd_server_fetch.argtypes = [P, LL, P, P, I, P, I]
+            L.bsvd_server_release.argtypes = [P, LL]
+            L.bsvd_server_collect.argtypes = [P, I, I, P, P, P, P, P, P]
+            L.bsvd_server_pause.argtypes = [P, I]
+            L.bsvd_server_cancel.argtypes = [P]
+            L.bsvd_server_stats.argtypes = [P, P]
+            L.bsvd_server_destroy.argtypes = [P]
             _lib = L
     return _lib
 
@@ -297,3 +324,183 @@ def autotune(A: torch.Tensor, compute_u: bool = True, compute_v: bool = True, *,
     names = ["fused", "blocked"] * 4
     tt = {(names[c], nbs[c]): times[c] for c in range(8) if times[c] >= 0}
     return {"path": PATH_NAMES[best.path], "nb": best.nb}, tt
+
+
+STATS_KEYS = ("submitted", "completed", "failed", "queued", "running", "running_batches", "arena_used",
+              "arena_peak", "cancelled", "batches")
+
+
+class Server:
+    """Continuous-batching SVD server on a CUDA device (``bsvd_server_*`` in
+    include/bsvd.h): single-matrix requests are queued, batched by type and
+    block width, admitted within a device-memory arena of ``arena_bytes``
+    (allocated here with torch and owned by this object) and solved by the
+    persistent kernel, each request completing as soon as its matrix has.
+
+    Inputs must be CUDA tensors or page-locked CPU tensors (a pageable CPU
+    tensor is copied to page-locked memory first); they are kept alive here
+    until their request is released.
+    """
+
+    def __init__(self, arena_bytes: int, *, max_inflight: int = 0, max_batch: int = 0, big_k: int = 0,
+                 max_big_batch: int = 0, device=None):
+        self.lib = load()
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=dev)
+        o = ServerOpts()
+        o.max_inflight, o.max_batch, o.big_k = int(max_inflight), int(max_batch), int(big_k)
+        o.max_big_batch = int(max_big_batch)
+        srv = ctypes.c_void_p()
+        with torch.cuda.device(dev):
+            st = self.lib.bsvd_server_create(self.arena.data_ptr(), self.arena.numel(), ctypes.byref(o),
+                                             ctypes.byref(srv))
+        if st != BSVD_OK:
+            raise BsvdError(st, "bsvd_server_create")
+        self.srv = srv
+        self._keep = {}
+        self._meta = {}
+
+    # -- requests --------------------------------------------------------
+    def _input(self, A: torch.Tensor) -> torch.Tensor:
+        if A.dim() != 2 or A.dtype not in DTYPES:
+            raise TypeError("a request is one 2-D float32/float64/complex64/complex128 matrix")
+        A = column_major(A.unsqueeze(0))[0]
+        if not A.is_cuda and not A.is_pinned():
+            A = A.t().contiguous().pin_memory().t()       # column-major, page-locked
+        return A
+
+    def submit(self, A: torch.Tensor, compute_u: bool = True, compute_v: bool = True) -> int:
+        A = self._input(A)
+        m, n = A.shape
+        rid = ctypes.c_longlong()
+        st = self.lib.bsvd_server_submit(self.srv, DTYPES[A.dtype].encode(), m, n, A.data_ptr(),
+                                         leading_dim(A), int(compute_u), int(compute_v), ctypes.byref(rid))
+        if st != BSVD_OK:
+            raise BsvdError(st, "bsvd_server_submit")
+        self._keep[rid.value] = A
+        self._meta[rid.value] = (A.dtype, m, n, compute_u, compute_v)
+        return rid.value
+
+    def replay(self, t_offset, mats, compute_u: bool = True, compute_v: bool = True, keep: bool = True):
+        """Submit mats[i] at t0 + t_offset[i] (seconds) from the calling thread,
+        each stamped with its scheduled time; returns (ids, t0).  With
+        keep=False the caller keeps the inputs alive until their requests
+        complete (and fetch() is not available for them)."""
+        import numpy as np
+        seen = {}
+        mats = [seen[id(A)] if id(A) in seen else seen.setdefault(id(A), self._input(A)) for A in mats]
+        B = len(mats)
+        t = np.ascontiguousarray(np.asarray(t_offset, dtype=np.float64))
+        dt = np.frombuffer(b"".join(DTYPES[A.dtype].encode() for A in mats), dtype=np.uint8).copy()
+        m = np.array([A.shape[0] for A in mats], dtype=np.int32)
+        n = np.array([A.shape[1] for A in mats], dtype=np.int32)
+        lda = np.array([leading_dim(A) for A in mats], dtype=np.int32)
+        ptr = np.array([A.data_ptr() for A in mats], dtype=np.uint64)
+        ids = np.zeros(B, dtype=np.int64)
+        t0 = ctypes.c_double()
+        st = self.lib.bsvd_server_replay(self.srv, B, t.ctypes.data, dt.ctypes.data, m.ctypes.data, n.ctypes.data,
+                                         ptr.ctypes.data, lda.ctypes.data, int(compute_u), int(compute_v),
+                                         ids.ctypes.data, ctypes.byref(t0))
+        for i, A in zip(ids.tolist(), mats if keep else []):
+            if i > 0 and self.lib.bsvd_server_test(self.srv, i) >= 0:    # not collected and released yet
+                self._keep[i] = A
+                self._meta[i] = (A.dtype, A.shape[0], A.shape[1], compute_u, compute_v)
+        if st != BSVD_OK:
+            raise BsvdError(st, "bsvd_server_replay")
+        return ids, t0.value
+
+    def test(self, rid: int) -> int:
+        return self.lib.bsvd_server_test(self.srv, rid)
+
+    def wait(self, rid: int, timeout: float = -1.0):
+        """Block until request rid completes; returns (info, sweeps, t_done)."""
+        info, sweeps, t_done = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        st = self.lib.bsvd_server_wait(self.srv, rid, float(timeout), ctypes.byref(info), ctypes.byref(sweeps),
+                                       ctypes.byref(t_done))
+        if st != BSVD_OK:
+            raise BsvdError(st, "bsvd_server_wait")
+        return info.value, sweeps.value, t_done.value
+
+    def fetch(self, rid: int, device="cpu", release: bool = True) -> SVDResult:
+        """Copy request rid's results into new tensors on `device` (waits for it)."""
+        info, sweeps, _ = self.wait(rid)
+        dt, m, n, cu, cv = self._meta[rid]
+        k = min(m, n)
+        dev = torch.device(device)
+        S = torch.empty(k, dtype=REAL[dt], device=dev)
+        U = torch.empty((k, m), dtype=dt, device=dev).t() if cu else None
+        V = torch.empty((k, n), dtype=dt, device=dev).t() if cv else None
+        st = self.lib.bsvd_server_fetch(self.srv, rid, S.data_ptr(), U.data_ptr() if cu else None, max(m, 1),
+                                        V.data_ptr() if cv else None, max(n, 1))
+        if st != BSVD_OK:
+            raise BsvdError(st, "bsvd_server_fetch")
+        if release:
+            self.release(rid)
+        return SVDResult(S, U, V, info, sweeps)
+
+    def release(self, rid: int):
+        st = self.lib.bsvd_server_release(self.srv, rid)
+        if st != BSVD_OK:
+            raise BsvdError(st, "bsvd_server_release")
+        self._keep.pop(rid, None)
+        self._meta.pop(rid, None)
+
+    def collect(self, max_count: int = 65536, release: bool = True):
+        """Requests completed since the last collect: dict of numpy arrays
+        id, status, info, sweeps, t_submit, t_done (released if asked)."""
+        import numpy as np
+        out = {"id": np.zeros(max_count, np.int64), "status": np.zeros(max_count, np.int32),
+               "info": np.zeros(max_count, np.int32), "sweeps": np.zeros(max_count, np.int32),
+               "t_submit": np.zeros(max_count, np.float64), "t_done": np.zeros(max_count, np.float64)}
+        k = self.lib.bsvd_server_collect(self.srv, max_count, int(release), *(out[x].ctypes.data for x in
+                                         ("id", "status", "info", "sweeps", "t_submit", "t_done")))
+        if k < 0:
+            raise BsvdError(k, "bsvd_server_collect")
+        out = {key: v[:k] for key, v in out.items()}
+        if release:
+            for i in out["id"].tolist():
+                self._keep.pop(i, None)
+                self._meta.pop(i, None)
+        return out
+
+    def cancel(self):
+        """Cancel queued requests and stop running persistent batches early."""
+        _ok(self.lib.bsvd_server_cancel(self.srv), "bsvd_server_cancel")
+
+    def pause(self, paused: bool = True):
+        _ok(self.lib.bsvd_server_pause(self.srv, int(paused)), "bsvd_server_pause")
+
+    def stats(self) -> dict:
+        c = (ctypes.c_longlong * 10)()
+        _ok(self.lib.bsvd_server_stats(self.srv, ctypes.cast(c, ctypes.c_void_p)), "bsvd_server_stats")
+        return dict(zip(STATS_KEYS, list(c)))
+
+    def clock(self) -> float:
+        return self.lib.bsvd_server_clock()
+
+    def close(self):
+        if getattr(self, "srv", None):
+            st = self.lib.bsvd_server_destroy(self.srv)
+            self.srv = None
+            self._keep.clear()
+            self._meta.clear()
+            if st != BSVD_OK:
+                raise BsvdError(st, "bsvd_server_destroy")
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ok(st: int, where: str):
+    if st != BSVD_OK:
+        raise BsvdError(st, where)

@@ -6,6 +6,7 @@ library lands next to this file.  No cmake, no torch extension machinery.
 from __future__ import annotations
 
 import os
+import platform
 import shutil
 import subprocess
 from concurrent.futures import ThreadPoolExecutor
@@ -19,7 +20,7 @@ LIB = os.path.join(HERE, "libbsvd.so")
 
 SOURCES = ["bsvd_api.cu", "fused_s.cu", "fused_d.cu", "fused_c.cu", "fused_z.cu",
            "blocked_s.cu", "blocked_d.cu", "blocked_c.cu", "blocked_z.cu", "noalloc_d.cu",
-           "mixed.cu"]
+           "mixed.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          f"-I{INCLUDE}", f"-I{CSRC}"]
@@ -52,9 +53,24 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     flags = FLAGS + (extra_flags or [])
+    # objects are reused only if built on this machine type with these flags
+    # and newer than their source and every header
+    stamp_path = os.path.join(BUILD, "stamp.txt")
+    stamp = " ".join([platform.machine(), cc, *ARCH, *flags])
+    old = open(stamp_path).read() if os.path.exists(stamp_path) else ""
+    headers = [f for f in _deps() if not f.endswith(".cu")] + [__file__]
+    newest_header = max(os.path.getmtime(f) for f in headers)
+
+    def fresh(src: str, obj: str) -> bool:
+        if force or old != stamp or not os.path.exists(obj):
+            return False
+        t = os.path.getmtime(obj)
+        return t >= os.path.getmtime(os.path.join(CSRC, src)) and t >= newest_header
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        if fresh(src, obj):
+            return obj
         cmd = [cc, *ARCH, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
@@ -65,8 +81,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
+    with open(stamp_path, "w") as f:
+        f.write(stamp)
     tmp = f"{LIB}.{os.getpid()}.tmp"
-    res = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+    res = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"], capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
     os.replace(tmp, LIB)

@@ -495,7 +495,8 @@ bsvd_status persistent_impl(bsvd_handle h, const TypeOps& ops, bool wantU, bool 
                             const int* m, const int* n, const void* const* dA, const int* lda,
                             void* const* dS, void* const* dU, const int* ldu, void* const* dV,
                             const int* ldv, int* d_info, int* d_sweeps, void* d_work,
-                            size_t work_bytes, const bsvd_opts* opts, cudaStream_t s) {
+                            size_t work_bytes, const bsvd_opts* opts, cudaStream_t s, int* d_done = nullptr,
+                            const int* d_abort = nullptr) {
     PersistPlan pp;
     bsvd_status st = plan_persistent(h->sm_count, ops, batch, m, n, opts, pp);
     if (st != BSVD_OK) return st;
@@ -539,6 +540,8 @@ bsvd_status persistent_impl(bsvd_handle h, const TypeOps& ops, bool wantU, bool 
     p.head = dws + 6 * batch;
     p.ws = static_cast<char*>(d_work) + pp.ints;
     p.slot_elems = pp.slot;
+    p.done = d_done;
+    p.abort = d_abort;
     e = ops.persist(pp.nb, p, pp.grid, pp.maxN, s);
     return e == cudaSuccess ? BSVD_OK : fail_cuda(h, e);
 }
@@ -660,6 +663,18 @@ size_t bsvd::blocked_bytes(int nb, int M, int N, int count, bool two_stage, size
     return blk_bytes(nb, M, N, count, two_stage, elt);
 }
 
+bsvd_status bsvd::persistent_with_flags(bsvd_handle h, char t, bool wantU, bool wantV, int batch, const int* m,
+                                        const int* n, const void* const* dA, const int* lda, void* const* dS,
+                                        void* const* dU, const int* ldu, void* const* dV, const int* ldv,
+                                        int* d_info, int* d_sweeps, int* d_done, const int* d_abort,
+                                        void* d_work, size_t work_bytes, const bsvd_opts* opts, cudaStream_t s) {
+    if (!h || batch < 1) return BSVD_ERR_INVALID;
+    bsvd_status st = refresh_device(h);
+    if (st != BSVD_OK) return st;
+    return persistent_impl(h, ops_for(t), wantU, wantV, batch, m, n, dA, lda, dS, dU, ldu, dV, ldv, d_info,
+                           d_sweeps, d_work, work_bytes, opts, s, d_done, d_abort);
+}
+
 namespace {
 
 // Candidates of the autotuner: block width x {on-chip fused, multi-kernel}.
@@ -738,6 +753,7 @@ const char* bsvd_status_string(bsvd_status s) {
         case BSVD_ERR_TIMEOUT: return "BSVD_ERR_TIMEOUT: a bounded device wait expired";
         case BSVD_ERR_NOT_IMPLEMENTED: return "BSVD_ERR_NOT_IMPLEMENTED: shape/type/option not supported";
         case BSVD_ERR_NOMEM: return "BSVD_ERR_NOMEM: host allocation failed";
+        case BSVD_ERR_CANCELLED: return "BSVD_ERR_CANCELLED: request cancelled";
     }
     return "unknown bsvd_status";
 }

@@ -322,7 +322,11 @@ gesvj_fused_kernel(const FusedArgs a) {
 // Pointer-array batches of any shapes in one persistent launch: each CTA
 // takes the next matrix from a work queue (ids in `order`, largest first),
 // lays it out in its own global-memory slot and solves it with the same
-// per-matrix code as the on-chip kernel.
+// per-matrix code as the on-chip kernel.  With `done` given, the CTA raises
+// done[id] once matrix id's outputs are written, so a host that polls the
+// flags can hand each result out before the launch ends; with `abort` given,
+// a CTA that finds it set takes no further matrix (those not started keep
+// their done flag at zero).
 struct PersistArgs {
     FusedArgs base;            // outputs, options, jobs and shared-memory offsets
     const int* mm;             // m of each matrix (by id)
@@ -332,7 +336,16 @@ struct PersistArgs {
     int* head;                 // queue head, zero at launch
     void* ws;                  // gridDim.x slots of slot_elems elements
     long long slot_elems;
+    int* done;                 // per-id completion flags (host-mapped memory) or nullptr
+    const int* abort;          // nonzero: take no further matrix (host-mapped) or nullptr
 };
+
+// Release store at system scope: every write this CTA made before the barrier
+// that precedes it (each writer fenced at system scope) is visible to the host
+// before the flag is.
+__device__ __forceinline__ void store_release_sys(int* p, int v) {
+    asm volatile("st.release.sys.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 template <class T, int NB, int NG, int GT>
 __global__ void __launch_bounds__(NG * GT, fused_min_blocks<T>())
@@ -342,8 +355,12 @@ gesvj_persistent_kernel(const PersistArgs p) {
     T* const slot = static_cast<T*>(p.ws) + (long long)blockIdx.x * p.slot_elems;
     for (;;) {
         if (threadIdx.x == 0) {
-            const int k = atomicAdd(p.head, 1);
-            s_mid = k < p.count ? p.order[k] : -1;
+            if (p.abort && *reinterpret_cast<const volatile int*>(p.abort)) {
+                s_mid = -1;
+            } else {
+                const int k = atomicAdd(p.head, 1);
+                s_mid = k < p.count ? p.order[k] : -1;
+            }
         }
         __syncthreads();
         const int mid = s_mid;
@@ -355,7 +372,9 @@ gesvj_persistent_kernel(const PersistArgs p) {
         T* const W = slot;
         T* const Vs = slot + ((long long)a.ldw * a.Np + per16 - 1) / per16 * per16;
         fused_solve<T, NB, NG, GT>(a, mid, W, Vs, smem);
+        if (p.done) __threadfence_system();                // this thread's outputs before the flag
         __syncthreads();                                   // shared scratch reused next
+        if (p.done && threadIdx.x == 0) store_release_sys(p.done + mid, 1);
     }
 }
 

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include "bsvd.h"
+
 namespace bsvd {
 
 struct FusedArgs;
@@ -30,6 +32,16 @@ cudaError_t mixed_restore_z(const MixedArgs& a, int batch, cudaStream_t st);
 // Bytes of workspace the multi-kernel path needs for `count` matrices of one
 // shape (defined in bsvd_api.cu from the same layout as blocked_launch.cuh).
 size_t blocked_bytes(int nb, int M, int N, int count, bool two_stage, size_t elt);
+
+// The persistent launch of a pointer-array batch (as bsvd_?gesvj_batched with
+// path PERSISTENT) that also raises d_done[i] once matrix i's outputs are
+// written (d_done zeroed by the caller, typically host-mapped memory) and
+// starts no further matrix once *d_abort is nonzero (d_abort may be null).
+bsvd_status persistent_with_flags(bsvd_handle h, char t, bool wantU, bool wantV, int batch, const int* m,
+                                  const int* n, const void* const* dA, const int* lda, void* const* dS,
+                                  void* const* dU, const int* ldu, void* const* dV, const int* ldv,
+                                  int* d_info, int* d_sweeps, int* d_done, const int* d_abort,
+                                  void* d_work, size_t work_bytes, const bsvd_opts* opts, cudaStream_t s);
 
 #define BSVD_DECLARE_FUSED(TAG)                                                          \
     size_t fused_plan_##TAG(int nb, int M, int N, bool needVs, FusedArgs& a, int& nt);  \

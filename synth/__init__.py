@@ -191,3 +191,57 @@ def random01(rng: np.random.Generator, m: int, n: int, dtype=np.float64) -> np.n
     if np.issubdtype(np.dtype(dtype), np.complexfloating):
         return (rng.uniform(0, 1, (m, n)) + 1j * rng.uniform(0, 1, (m, n))).astype(dtype)
     return rng.uniform(0, 1, (m, n)).astype(dtype)
+
+
+# --------------------------------------------------------------------------
+# Serving stream: Poisson arrivals of single-matrix requests.
+# --------------------------------------------------------------------------
+SERVING = dict(seed=SEED_BASE + 5, rate=50000.0, seconds=10.0, m_lo=16, m_hi=1024, bins=64, variants=2,
+               dtypes=("s", "d", "c"), dtype_p=(0.5, 0.3, 0.2), kappa_lo=1e2, kappa_hi=1e6)
+_NP = {"s": np.float32, "d": np.float64, "c": np.complex64, "z": np.complex128}
+
+
+def serving_sizes(cfg: dict = SERVING) -> np.ndarray:
+    """The larger dimension of each size bin: log-spaced from m_lo to m_hi."""
+    return np.unique(np.rint(np.geomspace(cfg["m_lo"], cfg["m_hi"], cfg["bins"])).astype(int))
+
+
+def serving_shape(b: int, tall: bool, cfg: dict = SERVING) -> tuple[int, int]:
+    m = int(serving_sizes(cfg)[b])
+    return m, (-(-m // 2) if tall else m)
+
+
+def serving_matrix(b: int, tall: bool, t: str, v: int, cfg: dict = SERVING) -> np.ndarray:
+    """Pool matrix (size bin b, 2:1 tall or square, type t, variant v):
+    Q1 diag(sigma) Q2^H with Haar factors and logrand sigma (sigma_1 = 1,
+    sigma_n = 1/kappa, the rest log-uniform), kappa log-uniform in
+    [kappa_lo, kappa_hi]."""
+    m, n = serving_shape(b, tall, cfg)
+    key = ((b * 2 + int(tall)) * 4 + "sdcz".index(t)) * 64 + v
+    rng = rng_for(cfg["seed"], key)
+    kappa = float(np.exp(rng.uniform(np.log(cfg["kappa_lo"]), np.log(cfg["kappa_hi"]))))
+    sig = sigma_family("logrand", min(m, n), kappa, rng)
+    return with_sigma(rng, m, n, sig, t in "cz").astype(_NP[t])
+
+
+def serving_trace(rate: float, seconds: float, stream: int = 0, cfg: dict = SERVING) -> dict:
+    """Arrivals of a Poisson stream (seeded exponential gaps) over `seconds`:
+    per request its arrival offset t, size bin (m log-uniform in
+    [m_lo, m_hi], rounded to the nearest bin in log scale), shape (half
+    square, half 2:1 tall), type (by dtype_p) and pool variant."""
+    rng = rng_for(cfg["seed"] + 1, stream)
+    n_est = int(rate * seconds * 1.2 + 100)
+    t = np.cumsum(rng.exponential(1.0 / rate, n_est))
+    while t[-1] < seconds:
+        t = np.concatenate([t, t[-1] + np.cumsum(rng.exponential(1.0 / rate, n_est))])
+    t = t[t < seconds]
+    N = len(t)
+    lo, hi = np.log(cfg["m_lo"]), np.log(cfg["m_hi"])
+    u = rng.uniform(lo, hi, N)
+    sizes = serving_sizes(cfg)
+    ls = np.log(sizes)
+    b = np.searchsorted((ls[:-1] + ls[1:]) / 2, u)          # nearest bin in log scale
+    tall = rng.random(N) < 0.5
+    dt = rng.choice(len(cfg["dtypes"]), size=N, p=cfg["dtype_p"])
+    v = rng.integers(0, cfg["variants"], N)
+    return {"t": t, "bin": b, "tall": tall, "dtype": np.array(cfg["dtypes"])[dt], "variant": v}

@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(L):
 
 def test_version_and_status_strings(L):
     assert L.bsvd_version() == 1
-    for st in (0, -1, -2, -3, -4, -5, -6):
+    for st in (0, -1, -2, -3, -4, -5, -6, -7):
         assert L.bsvd_status_string(st).startswith(b"BSVD_")
 
 
@@ -129,3 +129,27 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(binding._build, "LIB", str(tmp_path / "absent.so"))
     with pytest.raises(RuntimeError, match="not built"):
         binding.load()
+
+
+def test_server_host_argument_checks(L):
+    """Server calls reject bad arguments before touching the device."""
+    srv = ctypes.c_void_p()
+    big = 1 << 30
+    assert L.bsvd_server_create(None, big, None, ctypes.byref(srv)) == -1           # no arena
+    assert L.bsvd_server_create(0x100001, big, None, ctypes.byref(srv)) == -1       # misaligned
+    assert L.bsvd_server_create(0x100000, 4096, None, ctypes.byref(srv)) == -1      # under 1 MiB
+    o = binding.ServerOpts()
+    o.max_inflight = 65
+    assert L.bsvd_server_create(0x100000, big, ctypes.byref(o), ctypes.byref(srv)) == -1
+    o.max_inflight, o.max_batch = 4, -1
+    assert L.bsvd_server_create(0x100000, big, ctypes.byref(o), ctypes.byref(srv)) == -1
+    assert L.bsvd_server_create(0x100000, big, None, None) == -1
+    rid = ctypes.c_longlong()
+    assert L.bsvd_server_submit(None, b"d", 4, 4, 0x1000, 4, 1, 1, ctypes.byref(rid)) == -1
+    assert L.bsvd_server_test(None, 1) == -1
+    assert L.bsvd_server_release(None, 1) == -1
+    assert L.bsvd_server_pause(None, 1) == -1
+    assert L.bsvd_server_cancel(None) == -1
+    assert L.bsvd_server_destroy(None) == -1
+    assert L.bsvd_server_collect(None, 4, 1, None, None, None, None, None, None) == -1
+    assert L.bsvd_server_clock() > 0
