@@ -372,6 +372,13 @@ def summarize_stream(tr, ids, t0, t_arrivals, t_stop, rec, idx, before, at_end, 
            "drained": bool(final["queued"] == 0 and final["running"] == 0),
            "drain_s": t_stop - t_arrivals, "info_nonzero": int((rec["info"][ok] != 0).sum()),
            "arena_peak_gb": final["arena_peak"] / 1e9}
+    bad = (rec["status"] != 0) & (rec["status"] != -7)
+    if bad.any():
+        codes, counts = np.unique(rec["status"][bad], return_counts=True)
+        out["failed_status"] = {str(int(c)): int(k) for c, k in zip(codes, counts)}
+        j = idx[bad][:5]
+        out["failed_examples"] = [[int(sizes[tr["bin"][i]]), bool(tr["tall"][i]), str(tr["dtype"][i]),
+                                   int(rec["info"][np.flatnonzero(idx == i)[0]])] for i in j]
     if not out["drained"] and out["throughput_rps"] > 0:
         out["left_at_stop"] = int(final["queued"] + final["running"])
         out["drain_estimate_s"] = out["left_at_stop"] / out["throughput_rps"]

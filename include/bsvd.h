@@ -99,7 +99,11 @@ typedef struct {
                           batch convergence).  Bits 1-2 with AUTO select the multi-kernel
                           path.
                           bit 3: no CUDA graph (the masked multi-kernel path otherwise
-                          records one sweep into a graph and replays it each sweep)    */
+                          records one sweep into a graph and replays it each sweep);
+                          bit 4: the masked multi-kernel path reads the batch's
+                          convergence on the host every 4 sweeps and launches no more
+                          sweeps once every matrix has converged (the call then
+                          synchronises `stream`; results are unchanged)                */
     int prec;          /* bsvd_prec; MIXED only for d/z and the strided form                 */
     int reserved[5];
 } bsvd_opts;
@@ -295,7 +299,8 @@ bsvd_status bsvd_server_replay(bsvd_server server, int count, const double* t_of
 int bsvd_server_test(bsvd_server server, long long id);
 
 /* Blocks until the request completes or timeout_s passes (< 0: no limit;
- * BSVD_ERR_TIMEOUT then).  info: as d_info of the batch calls; sweeps; t_done.
+ * BSVD_ERR_TIMEOUT then).  info: as d_info of the batch calls (for a request
+ * whose batch failed to launch with BSVD_ERR_CUDA, the cudaError_t); sweeps; t_done.
  * Any output pointer may be NULL.  Returns the request's status (see test). */
 bsvd_status bsvd_server_wait(bsvd_server server, long long id, double timeout_s, int* info, int* sweeps,
                              double* t_done);

@@ -13,8 +13,10 @@ masking, as hand-written CUDA kernels behind the C-ABI of include/bsvd.h.
 from .buildlib import build
 from .binding import (BsvdError, SVDResult, Server, gesvj, gesvj_batched, autotune, load, handle, make_opts,
                       column_major, empty_column_major, workspace_bytes, EXPORTS,
-                      FLAG_NO_V_CORRECTION, FLAG_TWO_STAGE, FLAG_NO_MASKS, FLAG_NO_GRAPH)
+                      FLAG_NO_V_CORRECTION, FLAG_TWO_STAGE, FLAG_NO_MASKS, FLAG_NO_GRAPH,
+                      FLAG_SYNC_CHECK)
 
 __all__ = ["build", "BsvdError", "SVDResult", "Server", "gesvj", "gesvj_batched", "autotune", "load", "handle",
            "make_opts", "column_major", "empty_column_major", "workspace_bytes", "EXPORTS",
-           "FLAG_NO_V_CORRECTION", "FLAG_TWO_STAGE", "FLAG_NO_MASKS", "FLAG_NO_GRAPH"]
+           "FLAG_NO_V_CORRECTION", "FLAG_TWO_STAGE", "FLAG_NO_MASKS", "FLAG_NO_GRAPH",
+           "FLAG_SYNC_CHECK"]

@@ -6,6 +6,7 @@
 
 #include "blocked_layout.h"
 #include "gesvj_blocked.cuh"
+#include "launch_util.cuh"
 #include "internal.h"
 
 namespace bsvd {
@@ -37,20 +38,15 @@ cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stag
 
     cudaError_t e;
     const int heevj_smem = 2 * TWO * LDG * (int)sizeof(T) + InnerTables<T, NB>::bytes();
-    e = cudaFuncSetAttribute(blk_heevj<T, NB, GT>, cudaFuncAttributeMaxDynamicSharedMemorySize, heevj_smem);
-    if (e != cudaSuccess) return e;
     const int fin_smem = (kBlkThreads / 32) * (int)sizeof(R) + 16 + 2 * (int)sizeof(T) +
                          a.N * ((int)sizeof(R) + 4) + 16;
-    e = cudaFuncSetAttribute(blk_finalize<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, fin_smem);
-    if (e != cudaSuccess) return e;
-
     const int upd_smem = TWO * TWO * (int)sizeof(T);
-    e = cudaFuncSetAttribute(blk_update_fused<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, upd_smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(blk_update_stage1<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, upd_smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(blk_update_stage2<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, upd_smem);
-    if (e != cudaSuccess) return e;
+    if ((e = allow_dynamic_smem<blk_heevj<T, NB, GT>>()) != cudaSuccess ||
+        (e = allow_dynamic_smem<blk_finalize<T>>()) != cudaSuccess ||
+        (e = allow_dynamic_smem<blk_update_fused<T, NB>>()) != cudaSuccess ||
+        (e = allow_dynamic_smem<blk_update_stage1<T, NB>>()) != cudaSuccess ||
+        (e = allow_dynamic_smem<blk_update_stage2<T, NB>>()) != cudaSuccess)
+        return e;
 
     blk_load<T><<<a.count, kBlkThreads, 0, st>>>(a);
     const dim3 gpair(a.count, z.L / 2);
@@ -96,9 +92,19 @@ cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stag
                       cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
             if (!graphed) cudaGetLastError();
         }
+        // flags bit 4: every kSyncEvery sweeps read the batch's any-active flag
+        // on the host and stop launching once every matrix has converged
+        constexpr int kSyncEvery = 4;
         for (int sw = 0; sw < a.max_sweeps; ++sw) {
             e = graphed ? cudaGraphLaunch(exec, st) : sweep(st);
             if (e != cudaSuccess) break;
+            if ((a.flags & 16) && sw % kSyncEvery == kSyncEvery - 1 && sw + 1 < a.max_sweeps) {
+                int any = 0;
+                if ((e = cudaMemcpyAsync(&any, a.any_active, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                    (e = cudaStreamSynchronize(st)) != cudaSuccess)
+                    break;
+                if (!any) break;
+            }
         }
         if (exec) cudaGraphExecDestroy(exec);   // freed once the queued launches finish
         if (graph) cudaGraphDestroy(graph);

@@ -100,7 +100,7 @@ bool resolve(const bsvd_opts* o, bool single, int N, Resolved& r) {
     std::memset(&z, 0, sizeof z);
     if (!o) o = &z;
     if (o->nb < 0 || o->max_sweeps < 0 || o->inner_sweeps < 0 || o->tol < 0 || o->path < 0 ||
-        o->path > BSVD_PATH_PERSISTENT || o->flags < 0 || o->flags > 15 || o->prec < 0 ||
+        o->path > BSVD_PATH_PERSISTENT || o->flags < 0 || o->flags > 31 || o->prec < 0 ||
         o->prec > BSVD_PREC_MIXED || (o->prec == BSVD_PREC_MIXED && single))
         return false;
     r.nb = o->nb ? o->nb : (N >= 48 ? 16 : (N >= 12 ? 8 : 4));

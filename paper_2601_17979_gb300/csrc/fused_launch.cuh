@@ -6,6 +6,7 @@
 
 #include "gesvj_fused.cuh"
 #include "internal.h"
+#include "launch_util.cuh"
 
 namespace bsvd {
 
@@ -70,8 +71,8 @@ size_t persist_smem_nb(int maxN, FusedArgs& a, int& nthreads) {
 template <class T, int NB>
 cudaError_t persist_launch_nb(const PersistArgs& p, int grid, size_t smem, cudaStream_t st) {
     using C = FusedCfg<NB>;
-    auto k = gesvj_persistent_kernel<T, NB, C::NG, C::GT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    constexpr auto k = gesvj_persistent_kernel<T, NB, C::NG, C::GT>;
+    cudaError_t e = allow_dynamic_smem<k>();
     if (e != cudaSuccess) return e;
     k<<<grid, C::NG * C::GT, smem, st>>>(p);
     return cudaGetLastError();
@@ -109,8 +110,8 @@ long long persist_slot(int nb, int m, int n) {
 template <class T, int NB>
 cudaError_t fused_launch_nb(const FusedArgs& a, int grid, size_t smem, cudaStream_t st) {
     using C = FusedCfg<NB>;
-    auto k = gesvj_fused_kernel<T, NB, C::NG, C::GT>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    constexpr auto k = gesvj_fused_kernel<T, NB, C::NG, C::GT>;
+    cudaError_t e = allow_dynamic_smem<k>();
     if (e != cudaSuccess) return e;
     k<<<grid, C::NG * C::GT, smem, st>>>(a);
     return cudaGetLastError();

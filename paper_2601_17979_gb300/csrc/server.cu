@@ -12,12 +12,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdint>
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -107,13 +109,18 @@ struct Request {
 // Batch key: type, jobs, block width; for the multi-kernel path also the shape.
 using Key = std::tuple<char, int, int, int, int, int>;   // dtype, jobs, nb, big, m, n
 
-struct Batch {
+// What a launch reads: the requests, their stream slot and the workspace.
+struct Job {
     std::vector<Request*> reqs;
-    std::vector<int> pending;      // indices of requests not yet retired
     bool persistent = true;
     int slot = -1;
     size_t ws_off = 0, ws_bytes = 0;
+};
+
+struct Batch : Job {
+    std::vector<int> pending;      // indices of requests not yet retired
     OutBlock* out = nullptr;
+    std::thread launcher;          // multi-kernel batches are launched off the worker thread
 };
 
 }  // namespace
@@ -131,6 +138,9 @@ struct bsvd_server_s {
     std::vector<bool> slot_busy;
     std::vector<bool> slot_abort;  // the slot's batch was told to stop
     std::vector<bool> slot_big;    // the slot runs a multi-kernel batch
+    std::vector<bsvd_handle> slot_h;                      // one library handle per stream
+    std::unique_ptr<std::atomic<int>[]> launch_state;     // per slot: 0 launching, 1 launched, < 0 failed
+    std::vector<int> launch_cuda;                         // per slot: cudaError_t of a failed launch
     int big_cap = 12;              // slots multi-kernel batches may hold at once
     cudaStream_t fetch_stream = nullptr;
 
@@ -167,6 +177,7 @@ bsvd_opts batch_opts(const Request* r0, bool persistent) {
     std::memset(&o, 0, sizeof o);
     o.nb = persistent ? auto_nb(r0->k) : 16;
     o.path = persistent ? BSVD_PATH_PERSISTENT : BSVD_PATH_AUTO;
+    o.flags = persistent ? 0 : 16;   // stop issuing sweeps once the batch has converged
     return o;
 }
 
@@ -208,8 +219,10 @@ void drop_out(bsvd_server_s* s, OutBlock*& ob) {
     ob = nullptr;
 }
 
-// Launch of one admitted batch (worker thread, without the mutex).
-bsvd_status launch(bsvd_server_s* s, Batch& bt) {
+// Launch of one admitted batch (without the mutex; the worker thread for
+// persistent batches, a launcher thread for multi-kernel ones, whose sweep
+// launches can block on a full launch queue).  Uses the slot's own handle.
+bsvd_status launch_impl(bsvd_server_s* s, const Job& bt, int& cuda_err) {
     const int B = (int)bt.reqs.size();
     const Request* r0 = bt.reqs.front();
     const char t = r0->dtype;
@@ -232,42 +245,65 @@ bsvd_status launch(bsvd_server_s* s, Batch& bt) {
     void* work = w + 4 * pa;
     const size_t work_bytes = bt.ws_bytes - 4 * pa;
     // pageable sources: each copy returns once its source is staged
-    if (cudaMemcpyAsync(dA, pA.data(), B * sizeof(void*), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(dS, pS.data(), B * sizeof(void*), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(dU, pU.data(), B * sizeof(void*), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(dV, pV.data(), B * sizeof(void*), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    cudaError_t ce = cudaMemcpyAsync(dA, pA.data(), B * sizeof(void*), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(dS, pS.data(), B * sizeof(void*), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(dU, pU.data(), B * sizeof(void*), cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(dV, pV.data(), B * sizeof(void*), cudaMemcpyHostToDevice, st);
+    if (ce != cudaSuccess) {
+        cuda_err = (int)ce;
         return BSVD_ERR_CUDA;
+    }
     int* df = s->dflags[bt.slot];
     const int MB = s->max_batch;
     const bsvd_opts o = batch_opts(r0, bt.persistent);
     const bsvd_job ju = r0->wantU ? BSVD_JOB_SOME : BSVD_JOB_NONE, jv = r0->wantV ? BSVD_JOB_SOME : BSVD_JOB_NONE;
     bsvd_status rc;
+    bsvd_handle h = s->slot_h[bt.slot];
     if (bt.persistent) {
-        rc = bsvd::persistent_with_flags(s->h, t, r0->wantU, r0->wantV, B, mm.data(), nn.data(), dA, lda.data(), dS,
+        rc = bsvd::persistent_with_flags(h, t, r0->wantU, r0->wantV, B, mm.data(), nn.data(), dA, lda.data(), dS,
                                          dU, ldu.data(), dV, ldv.data(), df, df + MB, df + 2 * MB, df + 3 * MB, work,
                                          work_bytes, &o, st);
     } else {
         switch (t) {
-            case 's': rc = bsvd_sgesvj_batched(s->h, ju, jv, B, mm.data(), nn.data(), (const float* const*)dA,
+            case 's': rc = bsvd_sgesvj_batched(h, ju, jv, B, mm.data(), nn.data(), (const float* const*)dA,
                                                lda.data(), (float* const*)dS, (float* const*)dU, ldu.data(),
                                                (float* const*)dV, ldv.data(), df, df + MB, work, work_bytes, &o, st);
                       break;
-            case 'd': rc = bsvd_dgesvj_batched(s->h, ju, jv, B, mm.data(), nn.data(), (const double* const*)dA,
+            case 'd': rc = bsvd_dgesvj_batched(h, ju, jv, B, mm.data(), nn.data(), (const double* const*)dA,
                                                lda.data(), (double* const*)dS, (double* const*)dU, ldu.data(),
                                                (double* const*)dV, ldv.data(), df, df + MB, work, work_bytes, &o, st);
                       break;
-            case 'c': rc = bsvd_cgesvj_batched(s->h, ju, jv, B, mm.data(), nn.data(), (const void* const*)dA,
+            case 'c': rc = bsvd_cgesvj_batched(h, ju, jv, B, mm.data(), nn.data(), (const void* const*)dA,
                                                lda.data(), (float* const*)dS, (void* const*)dU, ldu.data(),
                                                (void* const*)dV, ldv.data(), df, df + MB, work, work_bytes, &o, st);
                       break;
-            default:  rc = bsvd_zgesvj_batched(s->h, ju, jv, B, mm.data(), nn.data(), (const void* const*)dA,
+            default:  rc = bsvd_zgesvj_batched(h, ju, jv, B, mm.data(), nn.data(), (const void* const*)dA,
                                                lda.data(), (double* const*)dS, (void* const*)dU, ldu.data(),
                                                (void* const*)dV, ldv.data(), df, df + MB, work, work_bytes, &o, st);
                       break;
         }
     }
-    if (rc != BSVD_OK) return rc;
-    return cudaEventRecord(s->events[bt.slot], st) == cudaSuccess ? BSVD_OK : BSVD_ERR_CUDA;
+    if (rc != BSVD_OK) {
+        if (rc == BSVD_ERR_CUDA) cuda_err = bsvd_last_cuda(h);
+        return rc;
+    }
+    ce = cudaEventRecord(s->events[bt.slot], st);
+    cuda_err = (int)ce;
+    return ce == cudaSuccess ? BSVD_OK : BSVD_ERR_CUDA;
+}
+
+// Launches and records the outcome in the slot's launch state (and, for a
+// CUDA failure, the error code).
+void launch(bsvd_server_s* s, const Job& bt) {
+    int cuda_err = 0;
+    const bsvd_status rc = launch_impl(s, bt, cuda_err);
+    if (rc != BSVD_OK) {
+        cudaGetLastError();
+        cudaStreamSynchronize(s->streams[bt.slot]);   // work already queued
+        cudaGetLastError();
+    }
+    s->launch_cuda[bt.slot] = cuda_err;
+    s->launch_state[bt.slot].store(rc == BSVD_OK ? 1 : (int)rc, std::memory_order_release);
 }
 
 int load_acquire(const int* p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
@@ -281,6 +317,22 @@ void poll_running(bsvd_server_s* s) {
     for (size_t bi = 0; bi < s->running.size();) {
         Batch& bt = s->running[bi];
         const int* hf = s->hflags[bt.slot];
+        const int ls = s->launch_state[bt.slot].load(std::memory_order_acquire);
+        if (ls == 0) { ++bi; continue; }                  // its launcher is still issuing work
+        if (ls < 0) {
+            if (bt.launcher.joinable()) bt.launcher.join();
+            for (int i : bt.pending) {
+                bt.reqs[i]->info = s->launch_cuda[bt.slot];     // the cudaError_t, if any
+                complete(s, bt.reqs[i], ls);
+                s->in_flight--;
+            }
+            any = true;
+            s->arena->release(bt.ws_off, bt.ws_bytes);
+            drop_out(s, bt.out);
+            s->slot_busy[bt.slot] = false;
+            s->running.erase(s->running.begin() + bi);
+            continue;
+        }
         if (bt.persistent) {
             size_t w = 0;
             for (size_t j = 0; j < bt.pending.size(); ++j) {
@@ -313,6 +365,7 @@ void poll_running(bsvd_server_s* s) {
             s->in_flight--;
             any = true;
         }
+        if (bt.launcher.joinable()) bt.launcher.join();
         s->arena->release(bt.ws_off, bt.ws_bytes);
         drop_out(s, bt.out);
         s->slot_busy[bt.slot] = false;
@@ -407,25 +460,20 @@ void admit(bsvd_server_s* s, std::unique_lock<std::mutex>& lk) {
         s->slot_abort[slot] = false;
         std::memset(s->hflags[slot], 0, sizeof(int) * flag_ints(s));   // its previous batch has ended
         s->launched++;
-        lk.unlock();
-        const bsvd_status rc = launch(s, bt);
-        if (rc != BSVD_OK) {
-            cudaGetLastError();
-            cudaStreamSynchronize(s->streams[slot]);   // copies already queued
-            cudaGetLastError();
-        }
-        lk.lock();
-        if (rc != BSVD_OK) {
-            for (Request* r : bt.reqs) {
-                complete(s, r, rc);
-                s->in_flight--;
-            }
-            s->arena->release(bt.ws_off, bt.ws_bytes);
-            drop_out(s, bt.out);
-            s->slot_busy[slot] = false;
-            s->cv_done.notify_all();
+        if (!bt.persistent) {
+            s->launch_state[slot].store(0, std::memory_order_release);
+            const Job job = bt;                          // what the launcher reads
+            bt.launcher = std::thread([s, job]() {
+                cudaSetDevice(s->device);
+                launch(s, job);
+                s->cv_work.notify_one();
+            });
+            s->running.push_back(std::move(bt));
             continue;
         }
+        lk.unlock();
+        launch(s, bt);
+        lk.lock();
         s->running.push_back(std::move(bt));
     }
 }
@@ -555,6 +603,14 @@ bsvd_status bsvd_server_create(void* d_arena, size_t arena_bytes, const bsvd_ser
     s->slot_busy.assign(s->max_inflight, false);
     s->slot_abort.assign(s->max_inflight, false);
     s->slot_big.assign(s->max_inflight, false);
+    s->slot_h.assign(s->max_inflight, nullptr);
+    s->launch_cuda.assign(s->max_inflight, 0);
+    s->launch_state.reset(new (std::nothrow) std::atomic<int>[s->max_inflight]);
+    if (!s->launch_state) rc = BSVD_ERR_NOMEM;
+    for (int k = 0; k < s->max_inflight && rc == BSVD_OK; ++k) {
+        s->launch_state[k].store(1);
+        rc = bsvd_create(&s->slot_h[k]);
+    }
     s->big_cap = std::max(1, s->max_inflight - std::max(2, s->max_inflight / 4));
     for (int k = 0; k < s->max_inflight && rc == BSVD_OK; ++k) {
         void* hp = nullptr;
@@ -580,6 +636,8 @@ bsvd_status bsvd_server_create(void* d_arena, size_t arena_bytes, const bsvd_ser
             if (s->hflags[k]) cudaFreeHost(s->hflags[k]);
         }
         if (s->fetch_stream) cudaStreamDestroy(s->fetch_stream);
+        for (bsvd_handle hh : s->slot_h)
+            if (hh) bsvd_destroy(hh);
         if (s->h) bsvd_destroy(s->h);
         delete s->arena;
         delete s;
@@ -780,6 +838,7 @@ bsvd_status bsvd_server_destroy(bsvd_server s) {
         if (s->hflags[k]) cudaFreeHost(s->hflags[k]);
     }
     if (s->fetch_stream) cudaStreamDestroy(s->fetch_stream);
+    for (bsvd_handle hh : s->slot_h) bsvd_destroy(hh);
     bsvd_destroy(s->h);
     delete s->arena;
     delete s;

@@ -144,3 +144,14 @@ def test_caller_workspace_too_small_is_reported():
     work = torch.empty(64, dtype=torch.uint8, device="cuda")
     with pytest.raises(bsvd.BsvdError, match="WORKSPACE"):
         bsvd.gesvj(A, work=work)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_host_convergence_check_gives_same_bits(dtype):
+    """Flag bit 4 only stops launching sweeps after the batch converged."""
+    rng = np.random.default_rng(21)
+    mats = [rng.standard_normal((150, 100)).astype(dtype) for _ in range(6)]
+    S1, U1, V1, i1, w1 = run_gpu(mats, nb=16, path="blocked")
+    S2, U2, V2, i2, w2 = run_gpu(mats, nb=16, path="blocked", flags=bsvd.FLAG_SYNC_CHECK)
+    assert (i1 == 0).all() and np.array_equal(w1, w2)
+    assert np.array_equal(S1, S2) and np.array_equal(U1, U2) and np.array_equal(V1, V2)

@@ -235,3 +235,17 @@ def test_cancel_stops_queued_and_running_work():
         assert status.count(-7) == st["cancelled"] > 0
         A = rand(rng, 50, 40, "d")
         check_result(A, srv.fetch(srv.submit(pinned(A))), "after cancel")
+
+
+def test_concurrent_multi_kernel_batches():
+    """Multi-kernel batches of distinct shapes launch from several host
+    threads at once; every one completes within the bounds."""
+    rng = np.random.default_rng(19)
+    mats = [rand(rng, 70 + 9 * i, 66 + 7 * i, "sdc"[i % 3]) for i in range(12)]
+    with bsvd.Server(1024 * MiB, big_k=64) as srv:
+        srv.pause()
+        ids = [srv.submit(pinned(A)) for A in mats]
+        srv.pause(False)
+        for A, r in zip(mats, ids):
+            check_result(A, srv.fetch(r), f"{A.dtype} {A.shape}")
+        assert srv.stats()["failed"] == 0
