@@ -474,6 +474,57 @@ def serving_cpu_baseline(tr, small=300, large=8):
                       "OpenMP over matrices, weighted by the stream's mix"}
 
 
+def run_tallskinny(args, rank, world, local):
+    """Tall-skinny batches, n = 16 and m from 100 to 2,000, entries U[0,1]
+    (the paper's larnv inputs): the SVD with and without QR pre-processing."""
+    import torch
+    import paper_2601_17979_gb300 as bsvd
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    bsvd.build()
+    B = args.batch if args.batch != BATCH else 1000
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)    # larger than L2
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for t, dt in (("d", torch.float64), ("s", torch.float32), ("z", torch.complex128), ("c", torch.complex64)):
+        for m in (100, 200, 500, 1000, 1500, 2000):
+            rng = synth.rng_for(synth.SEED_BASE + 6, m * 4 + "sdcz".index(t))
+            x = rng.uniform(0, 1, (B, 16, m))
+            if t in "cz":
+                x = x + 1j * rng.uniform(0, 1, (B, 16, m))
+            A = torch.from_numpy(x).to(dt).to(dev).transpose(1, 2)      # column-major m x 16
+            row = {"dtype": t, "m": m, "n": 16, "batch": B}
+            for name, flags in (("noqr", 0), ("qr", bsvd.FLAG_QR)):
+                res = bsvd.gesvj(A, flags=flags)                         # warm-up
+                times = []
+                for _ in range(max(1, args.steps)):
+                    flush.fill_(1)
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    res = bsvd.gesvj(A, flags=flags)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(a.elapsed_time(b))
+                ms = statistics.median(times)
+                row[name + "_ms"] = ms
+                row[name + "_matrices_per_s"] = B / (ms * 1e-3)
+                row[name + "_info_nonzero"] = int((res.info != 0).sum().item())
+            row["qr_speedup"] = row["noqr_ms"] / row["qr_ms"]
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+    head = next(r for r in rows if r["dtype"] == "d" and r["m"] == 2000)
+    line = {"metric": "batch SVD matrices/s (tall-skinny 2000x16 FP64, QR pre-processing)",
+            "value": head["qr_matrices_per_s"], "unit": "matrices/s", "n_gpus": world, "steps": args.steps,
+            "warmup": 1, "ms_per_step": head["qr_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"tall-skinny: {B} matrices m x 16 per (type, m), m in 100..2000, entries "
+                                   "U[0,1] (real and imaginary parts); U, Sigma, V; median of steps",
+                       "l2": "L2 flushed (256 MB write) before every timed call"},
+            "results": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def config_dict(world, per_rank):
     return {"workload": "tall128x64: 10,000 FP64 (sigma geometric 1..1e-6) + 10,000 FP32 "
                         "(1..1e-3) matrices 128x64 = Q1 diag(sigma) Q2^T, Haar Q1, Q2",
@@ -495,10 +546,11 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 baseline path")
     ap.add_argument("--ladder", action="store_true", help="also time Design-2/3/4 (multi-kernel)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision FP64 leg")
-    ap.add_argument("--workload", default="tall128x64", choices=["tall128x64", "uneven", "serving"],
+    ap.add_argument("--workload", default="tall128x64", choices=["tall128x64", "uneven", "serving", "tallskinny"],
                     help="tall128x64 (default); uneven: 10,000 FP32 + 10,000 complex64 matrices, "
                          "m ~ U{8..512}, n ~ U{8..m}, one persistent launch per type; serving: a Poisson "
-                         "stream of single-matrix requests at the continuous-batching server")
+                         "stream of single-matrix requests at the continuous-batching server; tallskinny: "
+                         "n = 16, m = 100..2000, with and without QR pre-processing")
     ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (default 50,000)")
     ap.add_argument("--seconds", type=float, default=0.0, help="serving: stream length (default 10 s)")
     ap.add_argument("--drain", type=float, default=10.0, help="serving: seconds to drain after arrivals")
@@ -520,6 +572,9 @@ def main():
         return
     if args.workload == "serving":
         run_serving(args, rank, world, local)
+        return
+    if args.workload == "tallskinny":
+        run_tallskinny(args, rank, world, local)
         return
 
     import torch

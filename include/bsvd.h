@@ -103,7 +103,12 @@ typedef struct {
                           bit 4: the masked multi-kernel path reads the batch's
                           convergence on the host every 4 sweeps and launches no more
                           sweeps once every matrix has converged (the call then
-                          synchronises `stream`; results are unchanged)                */
+                          synchronises `stream`; results are unchanged);
+                          bit 5: QR pre-processing (Sec. "Pre-processing the SVD using a
+                          QR Factorization"; strided form, native precision): A = Q [R; 0]
+                          by Householder QR (of A^H when m < n), the SVD of the
+                          min(m, n)-square R by the path `path` selects, U = Q [U_R; 0].
+                          Workspace: bsvd_gesvj_workspace with the same options        */
     int prec;          /* bsvd_prec; MIXED only for d/z and the strided form                 */
     int reserved[5];
 } bsvd_opts;

@@ -20,6 +20,12 @@ Parity status (pins in ``tests/test_oracle_pins.py``):
 * ``rr_pair``         round-robin ordering -- pinned: the l = 4 sequence of
                       Sec. 5.1; every pair exactly once per sweep, disjoint
                       slots within a round.
+* ``gesvj_qr``        QR pre-processing (Sec. "Pre-processing the SVD using a
+                      QR Factorization"): Householder QR (numpy / LAPACK
+                      geqrf), the oracle's SVD of R, U = Q U_R -- pinned:
+                      sigma against Alg. 2 and LAPACK on tall, wide and square
+                      inputs, reconstruction and orthogonality, a planted
+                      mistake (U without Q) caught.
 """
 from __future__ import annotations
 
@@ -191,3 +197,44 @@ def blocked_rounds(A, nb, rounds, **kw):
 
 def gesvj(A, **kw):
     return default().gesvj(A, **kw)
+
+
+def gesvj_qr(A, **kw):
+    """SVD after QR pre-processing (Sec. "Pre-processing the SVD using a QR
+    Factorization"), for one matrix or a list.
+
+    A' = A (m >= n) or A^H (m < n) is factored A' = Q [R; 0] by Householder
+    QR (numpy's reduced QR, LAPACK geqrf/orgqr: a library step), R is
+    decomposed by ``gesvj`` (same keyword arguments), and the left vectors of
+    A' are Q U_R; for m < n the roles of U and V swap back (A = V Sigma U^H
+    of A').  Returns the same dict as ``gesvj``.
+    """
+    single = isinstance(A, np.ndarray) and A.ndim == 2
+    mats = [A] if single else list(A)
+    Rs, Qs, trans = [], [], []
+    for a in mats:
+        cplx = np.iscomplexobj(a)
+        w = np.asarray(a).astype(np.complex128 if cplx else np.float64)
+        t = w.shape[0] < w.shape[1]
+        if t:
+            w = w.conj().T
+        Q, R = np.linalg.qr(w, mode="reduced")
+        Qs.append(Q)
+        Rs.append(R)
+        trans.append(t)
+    want_u, want_v = kw.pop("want_u", True), kw.pop("want_v", True)
+    r = default().gesvj(Rs, want_u=True, want_v=True, **kw)
+    S, U, V = [], [], []
+    for i, (Q, t) in enumerate(zip(Qs, trans)):
+        left = Q @ r["U"][i]            # left vectors of A'
+        right = r["V"][i]               # right vectors of A'
+        u, v = (right, left) if t else (left, right)
+        S.append(r["S"][i])
+        U.append(u)
+        V.append(v)
+    out = {"S": S, "U": U if want_u else None, "V": V if want_v else None, "sweeps": r["sweeps"],
+           "info": r["info"], "threads": r["threads"]}
+    if single:
+        return {"S": S[0], "U": U[0] if want_u else None, "V": V[0] if want_v else None,
+                "sweeps": int(r["sweeps"][0]), "info": int(r["info"][0]), "threads": r["threads"]}
+    return out

@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libbsvd.so")
 
 SOURCES = ["bsvd_api.cu", "fused_s.cu", "fused_d.cu", "fused_c.cu", "fused_z.cu",
            "blocked_s.cu", "blocked_d.cu", "blocked_c.cu", "blocked_z.cu", "noalloc_d.cu",
-           "mixed.cu", "server.cu"]
+           "mixed.cu", "server.cu", "qr.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          f"-I{INCLUDE}", f"-I{CSRC}"]

@@ -100,7 +100,7 @@ bool resolve(const bsvd_opts* o, bool single, int N, Resolved& r) {
     std::memset(&z, 0, sizeof z);
     if (!o) o = &z;
     if (o->nb < 0 || o->max_sweeps < 0 || o->inner_sweeps < 0 || o->tol < 0 || o->path < 0 ||
-        o->path > BSVD_PATH_PERSISTENT || o->flags < 0 || o->flags > 31 || o->prec < 0 ||
+        o->path > BSVD_PATH_PERSISTENT || o->flags < 0 || o->flags > 63 || o->prec < 0 ||
         o->prec > BSVD_PREC_MIXED || (o->prec == BSVD_PREC_MIXED && single))
         return false;
     r.nb = o->nb ? o->nb : (N >= 48 ? 16 : (N >= 12 ? 8 : 4));
@@ -351,6 +351,101 @@ bsvd_status mixed_impl(char t, bsvd_handle h, bool wantU, bool wantV, int batch,
     return e == cudaSuccess ? BSVD_OK : fail_cuda(h, e);
 }
 
+// ---- QR pre-processing (flags bit 5) ----------------------------------------
+constexpr int kFlagQR = 32;
+
+struct QrPlan {
+    Plan p;              // the SVD of R (N x N)
+    Resolved r;
+    size_t off[5];       // W, tau, R, ex, Uhat
+    size_t offp;         // the R-SVD's multi-kernel workspace
+    size_t bytes;
+};
+
+bsvd_status plan_qr(int max_smem, const TypeOps& ops, int m, int n, int batch, bool wantU, bool wantV,
+                    const Resolved& r, QrPlan& qp) {
+    const int M = std::max(m, n), N = std::min(m, n);
+    const bool trans = m < n;
+    const bool wy = trans ? wantV : wantU, wv = trans ? wantU : wantV;   // Q side, R's right side
+    qp.r = r;
+    qp.r.flags &= ~kFlagQR;
+    bsvd_status st = plan_group(max_smem, ops, N, N, batch, wy, wv, qp.r, qp.p);
+    if (st != BSVD_OK) return st;
+    const size_t b = (size_t)batch, e = ops.elt;
+    const size_t sizes[5] = {b * M * N * e, b * N * e, b * N * N * e, b * sizeof(int), wy ? b * N * N * e : 0};
+    size_t pos = 0;
+    for (int i = 0; i < 5; ++i) { qp.off[i] = pos; pos += align256(sizes[i]); }
+    qp.offp = pos;
+    if (qp.p.blocked) pos += align256(qp.p.bytes);
+    qp.bytes = pos;
+    return BSVD_OK;
+}
+
+// A' = Q [R; 0] (A' = A, or A^H when m < n), R = U_R Sigma V_R^H by the regular
+// paths, then the left vectors of A' are Q [U_R; 0] and its right ones V_R.
+bsvd_status qr_impl(char t, bsvd_handle h, bool wantU, bool wantV, int batch, int m, int n, const void* dA,
+                    int lda, long long sA, void* dS, long long sS, void* dU, int ldu, long long sU, void* dV,
+                    int ldv, long long sV, int* d_info, int* d_sweeps, void* d_work, size_t work_bytes,
+                    const Resolved& r, cudaStream_t s) {
+    const TypeOps ops = ops_for(t);
+    QrPlan qp;
+    bsvd_status st = plan_qr(h->max_smem, ops, m, n, batch, wantU, wantV, r, qp);
+    if (st != BSVD_OK) return st;
+    if (!d_work || work_bytes < qp.bytes) return BSVD_ERR_WORKSPACE;
+    const int M = std::max(m, n), N = std::min(m, n);
+    const bool trans = m < n;
+    const bool wy = trans ? wantV : wantU, wv = trans ? wantU : wantV;
+    char* w = static_cast<char*>(d_work);
+    bsvd::QrArgs qa;
+    std::memset(&qa, 0, sizeof qa);
+    qa.m = m; qa.n = n; qa.M = M; qa.N = N; qa.trans = trans;
+    qa.A = dA; qa.sA = sA; qa.lda = lda;
+    qa.W = w + qp.off[0]; qa.tau = w + qp.off[1]; qa.R = w + qp.off[2];
+    qa.ex = reinterpret_cast<int*>(w + qp.off[3]);
+    qa.Uhat = wy ? w + qp.off[4] : nullptr;
+    qa.Y = wy ? (trans ? dV : dU) : nullptr;
+    qa.sY = trans ? sV : sU;
+    qa.ldy = trans ? ldv : ldu;
+    qa.S = dS; qa.sS = sS;
+    cudaError_t e;
+    switch (t) {
+        case 's': e = bsvd::qr_factor_s(qa, batch, s); break;
+        case 'd': e = bsvd::qr_factor_d(qa, batch, s); break;
+        case 'c': e = bsvd::qr_factor_c(qa, batch, s); break;
+        default:  e = bsvd::qr_factor_z(qa, batch, s); break;
+    }
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    // the SVD of R: its U to the workspace, its V straight to the caller
+    void* pV = trans ? dU : dV;
+    const int pldv = trans ? ldu : ldv;
+    const long long psV = trans ? sU : sV;
+    if (qp.p.blocked) {
+        BlockedArgs a = blocked_args(N, N, batch, wy, wv, qp.r, qp.p.masks);
+        a.A = qa.R; a.sA = (long long)N * N; a.lda = N;
+        a.S = dS; a.sS = sS;
+        a.U = qa.Uhat; a.sU = (long long)N * N; a.ldu = N;
+        a.V = pV; a.sV = psV; a.ldv = pldv;
+        a.info = d_info; a.sweeps = d_sweeps;
+        e = ops.blocked(qp.p.nb, a, w + qp.offp, s, qp.p.two_stage, qp.p.host_sync, capture_stream(h, qp.r.flags));
+    } else {
+        FusedArgs& a = qp.p.a;
+        a.A = qa.R; a.sA = (long long)N * N; a.lda = N;
+        a.S = dS; a.sS = sS;
+        a.U = qa.Uhat; a.sU = (long long)N * N; a.ldu = N;
+        a.V = pV; a.sV = psV; a.ldv = pldv;
+        a.info = d_info; a.sweeps = d_sweeps;
+        e = ops.launch(qp.p.nb, a, batch, qp.p.smem, s);
+    }
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    switch (t) {
+        case 's': e = bsvd::qr_apply_s(qa, batch, s); break;
+        case 'd': e = bsvd::qr_apply_d(qa, batch, s); break;
+        case 'c': e = bsvd::qr_apply_c(qa, batch, s); break;
+        default:  e = bsvd::qr_apply_z(qa, batch, s); break;
+    }
+    return e == cudaSuccess ? BSVD_OK : fail_cuda(h, e);
+}
+
 bsvd_status strided_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, int batch, int m,
                          int n, const void* dA, int lda, long long sA, void* dS, long long sS,
                          void* dU, int ldu, long long sU, void* dV, int ldv, long long sV,
@@ -391,6 +486,11 @@ bsvd_status strided_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
         cudaError_t e = cudaMemsetAsync(d_info, 0, sizeof(int) * (size_t)batch, s);
         if (e == cudaSuccess && d_sweeps) e = cudaMemsetAsync(d_sweeps, 0, sizeof(int) * (size_t)batch, s);
         return e == cudaSuccess ? BSVD_OK : fail_cuda(h, e);
+    }
+    if (r.flags & kFlagQR) {
+        if (r.prec == BSVD_PREC_MIXED) return BSVD_ERR_NOT_IMPLEMENTED;
+        return qr_impl(t, h, wantU, wantV, batch, m, n, dA, lda, sA, dS, sS, dU, ldu, sU, dV, ldv, sV, d_info,
+                       d_sweeps, d_work, work_bytes, r, s);
     }
     if (r.prec == BSVD_PREC_MIXED)
         return mixed_impl(t, h, wantU, wantV, batch, m, n, dA, lda, sA, dS, sS, dU, ldu, sU, dV,
@@ -576,6 +676,7 @@ bsvd_status batched_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
     if (d_work && (reinterpret_cast<uintptr_t>(d_work) & 15) != 0) return fail_arg(h, 16);
     const TypeOps ops = ops_for(t);
     if (opts && opts->prec == BSVD_PREC_MIXED) return BSVD_ERR_NOT_IMPLEMENTED;   // strided form only
+    if (opts && (opts->flags & kFlagQR)) return BSVD_ERR_NOT_IMPLEMENTED;      // strided form only
     if (opts && opts->path == BSVD_PATH_PERSISTENT) {
         bsvd_status st = refresh_device(h);
         if (st != BSVD_OK) return st;
@@ -785,6 +886,13 @@ bsvd_status bsvd_gesvj_workspace(bsvd_handle handle, char dtype, int batch, cons
         if (!resolve(opts, ops.single, std::min(m, n), r)) return fail_arg(handle, 9);
         if (r.path == BSVD_PATH_PERSISTENT) r.path = BSVD_PATH_AUTO;   // as the strided call does
         apply_tuned(handle, dtype, m, n, wantU, wantV, opts, r);
+        if (r.flags & kFlagQR) {
+            if (r.prec == BSVD_PREC_MIXED) return BSVD_ERR_NOT_IMPLEMENTED;
+            QrPlan qp;
+            bsvd_status st = plan_qr(max_smem, ops, m, n, batch, wantU, wantV, r, qp);
+            if (st == BSVD_OK) *bytes = qp.bytes;
+            return st;
+        }
         if (r.prec == BSVD_PREC_MIXED) {
             MixedPlan mp;
             bsvd_status st = plan_mixed(max_smem, dtype, m, n, batch, wantU, wantV, r, mp);
@@ -804,6 +912,7 @@ bsvd_status bsvd_gesvj_workspace(bsvd_handle handle, char dtype, int batch, cons
         groups[{m_arr[i], n_arr[i]}].push_back(i);
     }
     if (opts && opts->prec == BSVD_PREC_MIXED) return BSVD_ERR_NOT_IMPLEMENTED;   // strided form only
+    if (opts && (opts->flags & kFlagQR)) return BSVD_ERR_NOT_IMPLEMENTED;      // strided form only
     if (opts && opts->path == BSVD_PATH_PERSISTENT) {
         PersistPlan pp;
         bsvd_status st = plan_persistent(device_sms_or_default(handle), ops, batch, m_arr, n_arr, opts, pp);

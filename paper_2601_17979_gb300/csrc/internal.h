@@ -24,6 +24,29 @@ struct MixedArgs {
     void* Ahat;                             // M x N, ld M, FP64: A V
 };
 
+// Buffers of the QR pre-processing path (strided batches; working
+// orientation M = max(m, n) rows, N = min(m, n) columns).
+struct QrArgs {
+    int m, n, M, N, trans;
+    const void* A; long long sA; int lda;   // the caller's A
+    void* W;                                // M x N, ld M: reflectors below the diagonal
+    void* tau;                              // N scalars per matrix
+    void* R;                                // N x N, ld N: the triangular factor
+    int* ex;                                // the power-of-two scaling of each matrix
+    void* Uhat;                             // N x N, ld N: left vectors of R
+    void* Y; long long sY; int ldy;         // Q [Uhat; 0]: the caller's U (V when m < n), or null
+    void* S; long long sS;                  // singular values, rescaled by 2^ex
+};
+
+cudaError_t qr_factor_s(const QrArgs& a, int batch, cudaStream_t st);
+cudaError_t qr_factor_d(const QrArgs& a, int batch, cudaStream_t st);
+cudaError_t qr_factor_c(const QrArgs& a, int batch, cudaStream_t st);
+cudaError_t qr_factor_z(const QrArgs& a, int batch, cudaStream_t st);
+cudaError_t qr_apply_s(const QrArgs& a, int batch, cudaStream_t st);
+cudaError_t qr_apply_d(const QrArgs& a, int batch, cudaStream_t st);
+cudaError_t qr_apply_c(const QrArgs& a, int batch, cudaStream_t st);
+cudaError_t qr_apply_z(const QrArgs& a, int batch, cudaStream_t st);
+
 cudaError_t mixed_prepare_d(const MixedArgs& a, int batch, cudaStream_t st);
 cudaError_t mixed_prepare_z(const MixedArgs& a, int batch, cudaStream_t st);
 cudaError_t mixed_restore_d(const MixedArgs& a, int batch, cudaStream_t st);

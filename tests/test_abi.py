@@ -153,3 +153,15 @@ def test_server_host_argument_checks(L):
     assert L.bsvd_server_destroy(None) == -1
     assert L.bsvd_server_collect(None, 4, 1, None, None, None, None, None, None) == -1
     assert L.bsvd_server_clock() > 0
+
+
+def test_qr_workspace_query(L):
+    """QR pre-processing needs workspace (reflectors, R, U_R) even where the
+    on-chip path alone needs none; the pointer-array form refuses it."""
+    plain = binding.workspace_bytes("d", [(1000, 16)], True, batch=10)
+    qr = binding.workspace_bytes("d", [(1000, 16)], True, batch=10, flags=binding.FLAG_QR)
+    assert qr >= 10 * (1000 * 16 + 16 + 16 * 16 + 16 * 16) * 8 > plain
+    with pytest.raises(binding.BsvdError, match="NOT_IMPLEMENTED"):
+        binding.workspace_bytes("d", [(1000, 16), (900, 16)], False, flags=binding.FLAG_QR)
+    with pytest.raises(binding.BsvdError, match="NOT_IMPLEMENTED"):
+        binding.workspace_bytes("d", [(1000, 16)], True, batch=2, flags=binding.FLAG_QR, prec="mixed")

@@ -319,3 +319,34 @@ def test_oracle_meets_bounds_on_workload_samples(O):
                 assert meas["orth_v"] <= 1.6 * checks.bounds(meas["n"], U)["orth_v"]
                 bad = [b for b in bad if b != "orth_v"]
             assert bad == [], (name, meas)
+
+
+# ---- QR pre-processing (Sec. "Pre-processing the SVD using a QR Factorization")
+@pytest.mark.parametrize("shape", [(300, 16), (1000, 16), (40, 40), (16, 200), (97, 37), (5, 1)])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_qr_path_matches_lapack_and_alg2(O, shape, cplx):
+    rng = np.random.default_rng(sum(shape) + 7)
+    A = rng.uniform(0, 1, shape)
+    if cplx:
+        A = A + 1j * rng.uniform(0, 1, shape)
+    r = oracle.gesvj_qr(A, tol=30 * U, nb=16 if min(shape) > 8 else 4)
+    assert r["info"] == 0
+    ref = np.linalg.svd(A, compute_uv=False)
+    meas = checks.measures(A, r["S"], r["U"], r["V"], ref)
+    assert checks.violations(meas, U) == [], meas
+    plain = O.gesvj(A, tol=30 * U)
+    assert np.abs(r["S"] - plain["S"]).max() <= 50 * min(shape) * U * ref[0]
+    assert r["U"].shape == (shape[0], min(shape)) and r["V"].shape == (shape[1], min(shape))
+
+
+def test_qr_path_planted_mistake_is_caught():
+    """Left vectors without Q (the R-SVD's U padded with zeros) fail the
+    reconstruction bound: the check sees the Q step."""
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((60, 12))
+    r = oracle.gesvj_qr(A, tol=30 * U)
+    _, R = np.linalg.qr(A)
+    wrong = np.zeros_like(r["U"])
+    wrong[:12] = (R @ r["V"]) / r["S"]          # left vectors of R, Q left out
+    meas = checks.measures(A, r["S"], wrong, r["V"], np.linalg.svd(A, compute_uv=False))
+    assert "resid" in checks.violations(meas, U)
