@@ -152,9 +152,36 @@ def gpu_uuid(torch, dev):
         return "0"
 
 
+def shard(rank: int, per_rank: int) -> range:
+    """Matrix indices of one rank: the ranks solve disjoint slices of the
+    seeded workload (weak scaling, no collective on the data path)."""
+    return range(rank * per_rank, (rank + 1) * per_rank)
+
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's time, i.e. the whole job's (one all-reduce of a
+    scalar after the timed region; nothing else crosses ranks)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, dist, device) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t)
+    return float(t.item())
+
+
 def build_inputs(rank: int, count: int):
-    A64 = synth.uniform_batch("tall128x64_f64", count, start=rank * count)
-    A32 = synth.uniform_batch("tall128x64_f32", count, start=rank * count)
+    idx = shard(rank, count)
+    A64 = synth.uniform_batch("tall128x64_f64", count, start=idx.start)
+    A32 = synth.uniform_batch("tall128x64_f32", count, start=idx.start)
     return A64, A32
 
 
@@ -205,8 +232,7 @@ def run_uneven(args, rank, world, local):
     torch.cuda.set_device(dev)
     bsvd.build()
     B = args.batch if args.batch != BATCH else 20000
-    ids = range(rank * B, (rank + 1) * B)
-    mats = synth.matrices("uneven", ids)
+    mats = synth.matrices("uneven", shard(rank, B))
     groups = {}
     for x in mats:
         groups.setdefault(x.dtype, []).append(x)
@@ -235,11 +261,7 @@ def run_uneven(args, rank, world, local):
             res = solve_all("persistent")
         b.record(stream)
         barrier()
-    ms = a.elapsed_time(b) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(a.elapsed_time(b) / args.steps, dist, dev)
     value = B * world / (ms * 1e-3)
     flops = 0.0
     for dt, r in res.items():
@@ -420,11 +442,7 @@ def run_serving(args, rank, world, local):
                       "submitted": s_["submitted"], "drained": s_["drained"]})
     batches = srv.stats()["batches"]
     srv.close()
-    value = main["throughput_rps"]
-    if dist is not None:
-        t = torch.tensor([value], device=dev, dtype=torch.float64)
-        dist.all_reduce(t)
-        value = float(t.item())
+    value = sum_over_ranks(main["throughput_rps"], dist, dev)
     sustained = [x["rate_rps"] for x in sweep if x["drained"] and x["completed"] == x["submitted"]]
     line = {"metric": "serving throughput (Poisson stream) with p50/p99 latency", "value": value,
             "unit": "requests/s", "n_gpus": world, "steps": 1, "warmup": args.warmup,
@@ -636,11 +654,7 @@ def main():
     total_ms = t_start.elapsed_time(t_end)
     k64 = [e[0].elapsed_time(e[1]) for e in evs]
     k32 = [e[1].elapsed_time(e[2]) for e in evs]
-    ms_step = total_ms / args.steps
-    if dist is not None:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(total_ms / args.steps, dist, dev)
     value = 2 * B * world / (ms_step * 1e-3)
 
     # results of the last step: convergence and a bounds check on a sample
@@ -738,11 +752,7 @@ def main():
             e2e_step()
         b.record(stream)
         barrier()
-        e_ms = a.elapsed_time(b) / args.steps
-        if dist is not None:
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms = max_over_ranks(a.elapsed_time(b) / args.steps, dist, dev)
         line["e2e"] = {"value": 2 * B * world / (e_ms * 1e-3), "unit": "matrices/s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                        "ms_per_step": e_ms}
