@@ -543,6 +543,80 @@ def run_tallskinny(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_mixed96(args, rank, world, local):
+    """The clustered 96x96 set: 2,000 real FP64 + 2,000 complex128 matrices,
+    sigma in 48 pairs with gap 1e-6, kappa about 1e8: FP64 output from FP32
+    sweeps + FP64 polish against native FP64 on the same inputs."""
+    import torch
+    import paper_2601_17979_gb300 as bsvd
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    bsvd.build()
+    per = args.batch if args.batch != BATCH else 4000
+    ids = shard(rank, per)
+    real = [synth.matrix("mixed96", i) for i in ids if i % 2 == 0]
+    cplx = [synth.matrix("mixed96", i) for i in ids if i % 2 == 1]
+    A = {"d": torch.from_numpy(np.stack(real)).to(dev).transpose(1, 2).contiguous().transpose(1, 2),
+         "z": torch.from_numpy(np.stack(cplx)).to(dev).transpose(1, 2).contiguous().transpose(1, 2)}
+    # 30 u, the default (the workload's n u = 96 u leaves U's orthogonality
+    # above the 20 n u gate at kappa 1e8, in the oracle as on the GPU)
+    tol = TOL_K * U64
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for prec in ("native", "mixed"):
+        for t in ("d", "z"):
+            bsvd.gesvj(A[t], nb=16, tol=tol, prec=prec)                 # warm-up
+        torch.cuda.synchronize()
+        times, res = {}, {}
+        for t in ("d", "z"):
+            ts = []
+            for _ in range(max(1, args.steps)):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                res[t] = bsvd.gesvj(A[t], nb=16, tol=tol, prec=prec)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            times[t] = statistics.median(ts)
+        total = max_over_ranks(times["d"] + times["z"], dist, dev)
+        worst = {}
+        for t, mats in (("d", real), ("z", cplx)):
+            r = res[t]
+            for i in range(0, len(mats), max(1, len(mats) // 8)):
+                Ah = mats[i]
+                S, U, V = r.S[i].cpu().numpy(), r.U[i].cpu().numpy(), r.V[i].cpu().numpy()
+                k = S.shape[0]
+                Ah = Ah.astype(np.complex128)
+                meas = {"resid": float(np.linalg.norm(Ah - (U * S) @ V.conj().T) / np.linalg.norm(Ah)),
+                        "orth_u": float(np.linalg.norm(U.conj().T @ U - np.eye(k))),
+                        "orth_v": float(np.linalg.norm(V.conj().T @ V - np.eye(k)))}
+                for key, val in meas.items():
+                    worst[key] = max(worst.get(key, 0.0), val / (20 * 96 * U64))
+        out[prec] = {"matrices_per_s": len(ids) * world / (total * 1e-3), "ms": total,
+                     "ms_real": times["d"], "ms_complex": times["z"],
+                     "sweeps_mean": {t: float(res[t].sweeps.float().mean().item()) for t in res},
+                     "info_nonzero": int(sum(int((res[t].info != 0).sum().item()) for t in res)),
+                     "accuracy_worst_over_bound": worst}
+    line = {"metric": "batch SVD matrices/s (96x96 clustered, FP64 output, mixed precision)",
+            "value": out["mixed"]["matrices_per_s"], "unit": "matrices/s", "n_gpus": world,
+            "steps": args.steps, "warmup": 1, "ms_per_step": out["mixed"]["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed), f64 output", "data": "synthetic",
+            "config": {"workload": f"mixed96: {per} square 96x96 per rank, even ids real FP64, odd ids complex128, "
+                                   "sigma in 48 clustered pairs (gap 1e-6), kappa 1e8, Haar factors",
+                       "nb": 16, "tol": "30 u", "jobs": "U, Sigma, V",
+                       "l2": "inputs (295 MB real + 590 MB complex per 4,000) larger than L2"},
+            "mixed": out["mixed"], "native_fp64": out["native"],
+            "speedup_over_native": out["native"]["ms"] / out["mixed"]["ms"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def config_dict(world, per_rank):
     return {"workload": "tall128x64: 10,000 FP64 (sigma geometric 1..1e-6) + 10,000 FP32 "
                         "(1..1e-3) matrices 128x64 = Q1 diag(sigma) Q2^T, Haar Q1, Q2",
@@ -564,11 +638,13 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 baseline path")
     ap.add_argument("--ladder", action="store_true", help="also time Design-2/3/4 (multi-kernel)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision FP64 leg")
-    ap.add_argument("--workload", default="tall128x64", choices=["tall128x64", "uneven", "serving", "tallskinny"],
+    ap.add_argument("--workload", default="tall128x64",
+                    choices=["tall128x64", "uneven", "serving", "tallskinny", "mixed96"],
                     help="tall128x64 (default); uneven: 10,000 FP32 + 10,000 complex64 matrices, "
                          "m ~ U{8..512}, n ~ U{8..m}, one persistent launch per type; serving: a Poisson "
                          "stream of single-matrix requests at the continuous-batching server; tallskinny: "
-                         "n = 16, m = 100..2000, with and without QR pre-processing")
+                         "n = 16, m = 100..2000, with and without QR pre-processing; mixed96: the clustered "
+                         "96x96 FP64/complex128 set, mixed precision against native FP64")
     ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (default 50,000)")
     ap.add_argument("--seconds", type=float, default=0.0, help="serving: stream length (default 10 s)")
     ap.add_argument("--drain", type=float, default=10.0, help="serving: seconds to drain after arrivals")
@@ -593,6 +669,9 @@ def main():
         return
     if args.workload == "tallskinny":
         run_tallskinny(args, rank, world, local)
+        return
+    if args.workload == "mixed96":
+        run_mixed96(args, rank, world, local)
         return
 
     import torch
