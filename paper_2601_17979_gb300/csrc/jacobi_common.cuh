@@ -71,23 +71,25 @@ template <class T, int NB>
 struct InnerTables {
     using R = Real<T>;
     struct Step { R* c; R* t; T* es; int* p; int* q; int* fired; };
-    Step step[2];
+    static constexpr int kStepBytes = NB * ((int)sizeof(T) + 2 * (int)sizeof(R) + 3 * 4);
+    char* base;
     int* count;   // [2]
-    __device__ explicit InnerTables(void* base) {
-        char* b = static_cast<char*>(base);
-        for (int k = 0; k < 2; ++k) {
-            step[k].es = reinterpret_cast<T*>(b);  b += NB * sizeof(T);
-            step[k].c = reinterpret_cast<R*>(b);   b += NB * sizeof(R);
-            step[k].t = reinterpret_cast<R*>(b);   b += NB * sizeof(R);
-            step[k].p = reinterpret_cast<int*>(b); b += NB * sizeof(int);
-            step[k].q = reinterpret_cast<int*>(b); b += NB * sizeof(int);
-            step[k].fired = reinterpret_cast<int*>(b); b += NB * sizeof(int);
-        }
-        count = reinterpret_cast<int*>(b);
+    __device__ explicit InnerTables(void* b)
+        : base(static_cast<char*>(b)), count(reinterpret_cast<int*>(static_cast<char*>(b) + 2 * kStepBytes)) {}
+    // Step k's arrays, by address arithmetic (an indexed array of pointer
+    // sets would live in local memory and cost a load per use)
+    __device__ __forceinline__ Step step(int k) const {
+        char* b = base + k * kStepBytes;
+        Step s;
+        s.es = reinterpret_cast<T*>(b);  b += NB * sizeof(T);
+        s.c = reinterpret_cast<R*>(b);   b += NB * sizeof(R);
+        s.t = reinterpret_cast<R*>(b);   b += NB * sizeof(R);
+        s.p = reinterpret_cast<int*>(b); b += NB * sizeof(int);
+        s.q = reinterpret_cast<int*>(b); b += NB * sizeof(int);
+        s.fired = reinterpret_cast<int*>(b);
+        return s;
     }
-    __host__ __device__ static constexpr int bytes() {
-        return 2 * NB * ((int)sizeof(T) + 2 * (int)sizeof(Real<T>) + 3 * 4) + 16;
-    }
+    __host__ __device__ static constexpr int bytes() { return 2 * kStepBytes + 16; }
 };
 
 // Below this, g_pp g_qq is not squared-compared (its square could underflow).
@@ -95,13 +97,41 @@ template <class R> constexpr R kJacobiProdMin = R(0);
 template <> constexpr float kJacobiProdMin<float> = 1e-30f;
 template <> constexpr double kJacobiProdMin<double> = 1e-280;
 
+// Products that the compiler may not fuse into a neighbouring add, and the
+// combinations c x + y e and c x - y e (c real) of the 2 x 2 rotations with
+// every rounding fixed by explicit FMAs: the inner solver then gives the same
+// bits in every kernel that inlines it, whatever the surrounding code.
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+
+__device__ __forceinline__ float rot_add(float x, float c, float y, float e) { return fmaf(y, e, __fmul_rn(x, c)); }
+__device__ __forceinline__ double rot_add(double x, double c, double y, double e) { return fma(y, e, __dmul_rn(x, c)); }
+__device__ __forceinline__ float2 rot_add(float2 x, float c, float2 y, float2 e) {
+    return make_float2(fmaf(y.x, e.x, fmaf(-y.y, e.y, __fmul_rn(x.x, c))),
+                       fmaf(y.x, e.y, fmaf(y.y, e.x, __fmul_rn(x.y, c))));
+}
+__device__ __forceinline__ double2 rot_add(double2 x, double c, double2 y, double2 e) {
+    return make_double2(fma(y.x, e.x, fma(-y.y, e.y, __dmul_rn(x.x, c))),
+                        fma(y.x, e.y, fma(y.y, e.x, __dmul_rn(x.y, c))));
+}
+__device__ __forceinline__ float rot_sub(float x, float c, float y, float e) { return fmaf(-y, e, __fmul_rn(x, c)); }
+__device__ __forceinline__ double rot_sub(double x, double c, double y, double e) { return fma(-y, e, __dmul_rn(x, c)); }
+__device__ __forceinline__ float2 rot_sub(float2 x, float c, float2 y, float2 e) {
+    return make_float2(fmaf(-y.x, e.x, fmaf(y.y, e.y, __fmul_rn(x.x, c))),
+                       fmaf(-y.x, e.y, fmaf(-y.y, e.x, __fmul_rn(x.y, c))));
+}
+__device__ __forceinline__ double2 rot_sub(double2 x, double c, double2 y, double2 e) {
+    return make_double2(fma(-y.x, e.x, fma(y.y, e.y, __dmul_rn(x.x, c))),
+                        fma(-y.x, e.y, fma(-y.y, e.x, __dmul_rn(x.y, c))));
+}
+
 // t = sign(x) y / (|x| + hypot(x, y)), y > 0.  FP32: sqrt and a fast division
 // (a couple of ulp) within the range where x^2 + y^2 neither overflows nor
 // underflows -- any t close to the exact one gives an orthogonal rotation,
 // since c = 1/sqrt(1 + t^2) and s = t c.  FP64: IEEE hypot and division.
 __device__ __forceinline__ float rotation_tan(float x, float y) {
     const float ax = fabsf(x), m = fmaxf(ax, y);
-    const float h = (m > 1e-18f && m < 1e18f) ? sqrtf(fmaf(x, x, y * y)) : hypotf(x, y);
+    const float h = (m > 1e-18f && m < 1e18f) ? sqrtf(fmaf(x, x, __fmul_rn(y, y))) : hypotf(x, y);
     const float yy = x >= 0.f ? y : -y;
     return (m > 1e-18f && m < 1e18f) ? __fdividef(yy, ax + h) : yy / (ax + h);
 }
@@ -124,10 +154,10 @@ __device__ __forceinline__ int inner_rotation(const T* G, Real<T> tol, int st, i
     const R apq = abs_s(gpq);
     // |g_pq| >= tol sqrt(g_pp) sqrt(g_qq), compared in squares while the
     // product stays well inside the normal range
-    const R prod = gpp * gqq;
+    const R prod = rmul(gpp, gqq);
     const bool fire = gpp > 0 && gqq > 0 && apq > 0 &&
-                      (prod > kJacobiProdMin<R> ? apq * apq >= tol * tol * prod
-                                                : apq >= tol * sqrt_r(gpp) * sqrt_r(gqq));
+                      (prod > kJacobiProdMin<R> ? rmul(apq, apq) >= rmul(rmul(tol, tol), prod)
+                                                : apq >= rmul(rmul(tol, sqrt_r(gpp)), sqrt_r(gqq)));
     R c = 1, t = 0;
     T es = make_s<T>(0);
     if (fire) {
@@ -135,7 +165,7 @@ __device__ __forceinline__ int inner_rotation(const T* G, Real<T> tol, int st, i
         // t = sign(tau) / (|tau| + sqrt(1 + tau^2)) = sign(x) y / (|x| + hypot(x, y))
         const R x = gpp - gqq, y = 2 * apq;
         t = rotation_tan(x, y);
-        c = rsqrt_r(R(1) + t * t);
+        c = rsqrt_r(fma_s(t, t, R(1)));
         es = scale(phase_s(gpq, apq), t * c);
     }
     out.c[slot] = c; out.t[slot] = t; out.es[slot] = es;
@@ -175,7 +205,7 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
     if (gt == 0) { tb.count[0] = 0; tb.count[1] = 0; }
     named_sync(bar, GT);
     if (gt < 32) {   // warp 0 forms the rotations; one ballot counts the fired ones
-        const int f = gt < NB ? inner_rotation<T, NB>(G, tol, 0, gt, tb.step[0]) : 0;
+        const int f = gt < NB ? inner_rotation<T, NB>(G, tol, 0, gt, tb.step(0)) : 0;
         const unsigned m = __ballot_sync(0xffffffffu, f);
         if (gt == 0) tb.count[0] += __popc(m);
     }
@@ -184,7 +214,7 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
     for (int isw = 0; isw < sweeps; ++isw) {
         for (int st = 0; st < STEPS; ++st) {
             const int gs = isw * STEPS + st;
-            const auto& cur = tb.step[gs & 1];
+            const auto cur = tb.step(gs & 1);
             // G <- R^H G R on 2x2 blocks (slot q1 <= slot q2), mirrored.  A
             // thread's blocks are disjoint: all loads first, then the math,
             // then the stores, so their latencies overlap.
@@ -214,26 +244,26 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
                     if (bq1[u] == bq2[u]) {
                         // diagonal block: closed form, off-diagonal set to zero
                         const R apq = abs_s(b01[u]);
-                        b00[u] = make_s<T>(re(b00[u]) + t1[u] * apq);
-                        b11[u] = make_s<T>(re(b11[u]) - t1[u] * apq);
+                        b00[u] = make_s<T>(fma_s(t1[u], apq, re(b00[u])));
+                        b11[u] = make_s<T>(fma_s(-t1[u], apq, re(b11[u])));
                         b01[u] = make_s<T>(0);
                         b10[u] = make_s<T>(0);
                         continue;
                     }
                     if (f2[u]) {   // columns (p2, r2) times R2
                         const T es = e2[u], ces = conj_s(es);
-                        const T n00 = add(scale(b00[u], c2[u]), mul(b01[u], ces));
-                        const T n01 = sub(scale(b01[u], c2[u]), mul(b00[u], es));
-                        const T n10 = add(scale(b10[u], c2[u]), mul(b11[u], ces));
-                        const T n11 = sub(scale(b11[u], c2[u]), mul(b10[u], es));
+                        const T n00 = rot_add(b00[u], c2[u], b01[u], ces);
+                        const T n01 = rot_sub(b01[u], c2[u], b00[u], es);
+                        const T n10 = rot_add(b10[u], c2[u], b11[u], ces);
+                        const T n11 = rot_sub(b11[u], c2[u], b10[u], es);
                         b00[u] = n00; b01[u] = n01; b10[u] = n10; b11[u] = n11;
                     }
                     if (f1[u]) {   // rows (p1, r1) times R1^H
                         const T es = e1[u], ces = conj_s(es);
-                        const T n00 = add(scale(b00[u], c1[u]), mul(es, b10[u]));
-                        const T n10 = sub(scale(b10[u], c1[u]), mul(ces, b00[u]));
-                        const T n01 = add(scale(b01[u], c1[u]), mul(es, b11[u]));
-                        const T n11 = sub(scale(b11[u], c1[u]), mul(ces, b01[u]));
+                        const T n00 = rot_add(b00[u], c1[u], b10[u], es);
+                        const T n10 = rot_sub(b10[u], c1[u], b00[u], ces);
+                        const T n01 = rot_add(b01[u], c1[u], b11[u], es);
+                        const T n11 = rot_sub(b11[u], c1[u], b01[u], ces);
                         b00[u] = n00; b01[u] = n01; b10[u] = n10; b11[u] = n11;
                     }
                 }
@@ -254,7 +284,7 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
             const bool last = (st + 1 == STEPS);
             if (gt < 32 && !(last && isw + 1 == sweeps)) {
                 const int nisw = last ? isw + 1 : isw;
-                const int f = gt < NB ? inner_rotation<T, NB>(G, tol, last ? 0 : st + 1, gt, tb.step[(gs + 1) & 1]) : 0;
+                const int f = gt < NB ? inner_rotation<T, NB>(G, tol, last ? 0 : st + 1, gt, tb.step((gs + 1) & 1)) : 0;
                 const unsigned m = __ballot_sync(0xffffffffu, f);
                 if (gt == 0) tb.count[nisw & 1] += __popc(m);
             }
@@ -282,8 +312,8 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
                 for (int u = 0; u < NJU; ++u)
                     if (fj[u]) {
                         const T es = ej[u], ces = conj_s(es);
-                        J[ij[u] + pj[u] * LDG] = add(scale(xj[u], cj[u]), mul(yj[u], ces));
-                        J[ij[u] + qj[u] * LDG] = sub(scale(yj[u], cj[u]), mul(xj[u], es));
+                        J[ij[u] + pj[u] * LDG] = rot_add(xj[u], cj[u], yj[u], ces);
+                        J[ij[u] + qj[u] * LDG] = rot_sub(yj[u], cj[u], xj[u], es);
                     }
             }
             named_sync(bar, GT);
