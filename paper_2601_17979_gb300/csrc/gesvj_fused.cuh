@@ -266,21 +266,23 @@ __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T
                         T* X = W;
                         int ld = ldw, row = i;
                         if (i >= M) { X = Vs; ld = ldvs; row = i - M; }
-                        T x[TWO];
+                        // nb accumulators, each summed over k in order (the
+                        // multi-kernel path's order); x is read one k at a time
+                        T acc[NB];
+#pragma unroll
+                        for (int c = 0; c < NB; ++c) acc[c] = make_s<T>(0);
                         if (ok) {
 #pragma unroll
-                            for (int k = 0; k < TWO; ++k) x[k] = X[row + col(k) * ld];
+                            for (int k = 0; k < TWO; ++k) {
+                                const T xk = X[row + col(k) * ld];
+#pragma unroll
+                                for (int c = 0; c < NB; ++c) acc[c] = fma_s(xk, J[k + (half * NB + c) * LDG], acc[c]);
+                            }
                         }
                         __syncwarp();
                         if (ok) {
 #pragma unroll
-                            for (int c = 0; c < NB; ++c) {
-                                const int cc = half * NB + c;
-                                T acc = make_s<T>(0);
-#pragma unroll
-                                for (int k = 0; k < TWO; ++k) acc = fma_s(x[k], J[k + cc * LDG], acc);
-                                X[row + col(cc) * ld] = acc;
-                            }
+                            for (int c = 0; c < NB; ++c) X[row + col(half * NB + c) * ld] = acc[c];
                         }
                     }
                 }
