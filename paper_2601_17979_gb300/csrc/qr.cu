@@ -9,15 +9,23 @@
 // kQrChunk columns: one sweep over the rows accumulates v^H W for the whole
 // chunk, one block reduction, one sweep applies the rank-1 update.  Q is
 // never formed; qr_apply applies H_{N-1}, ..., H_0 to [U_R; 0] in turn.
+// Where the matrix fits (at most 2,048 rows and the kQrSmemMax bytes below),
+// the factorization works on a copy in shared memory and the application
+// keeps Y there, staging each reflector through a double buffer that is
+// filled while the previous reflector is applied; otherwise both work on
+// L2-resident global buffers.
 #include <cuda_runtime.h>
 
 #include "internal.h"
 #include "jacobi_common.cuh"
+#include "launch_util.cuh"
 
 namespace bsvd {
 
 constexpr int kQrThreads = 256;
 constexpr int kQrChunk = 16;
+constexpr int kQrSmemMax = 200 * 1024;
+constexpr int kQrRowsPerThread = 8;                        // the shared-memory variants: M <= 2,048
 
 __device__ __forceinline__ float im_s(float) { return 0.f; }
 __device__ __forceinline__ double im_s(double) { return 0.0; }
@@ -78,24 +86,24 @@ __device__ __forceinline__ R block_sum_r(R v, R* red) {
     return t;
 }
 
-// X(j:M, k0:k0+nk) -= f v (v^H X(j:M, k0:k0+nk)), v(j) = 1 and v(i > j) in
-// column j of W; f is conj(tau) for H^H and tau for H.
+// X(j:M, k0:k0+nk) -= f v (v^H X(j:M, k0:k0+nk)), v(j) = 1 and v(i > j) =
+// v[i]; f is conj(tau) for H^H and tau for H.
 template <class T>
-__device__ __forceinline__ void apply_reflector(const T* W, int M, int j, T f, T* X, int ldx, int k0, int nk,
+__device__ __forceinline__ void apply_reflector(const T* v_col, int M, int j, T f, T* X, int ldx, int k0, int nk,
                                                 T* red, T* sh) {
     constexpr int NT = kQrThreads, CH = kQrChunk;
     T acc[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) acc[c] = make_s<T>(0);
     for (int i = j + threadIdx.x; i < M; i += NT) {
-        const T v = i == j ? make_s<T>(1) : W[i + (long long)j * M];
+        const T v = i == j ? make_s<T>(1) : v_col[i];
 #pragma unroll
         for (int c = 0; c < CH; ++c)
             if (c < nk) acc[c] = cfma(v, X[i + (long long)(k0 + c) * ldx], acc[c]);
     }
     block_sum<T, CH>(acc, red, sh);
     for (int i = j + threadIdx.x; i < M; i += NT) {
-        const T v = i == j ? make_s<T>(1) : W[i + (long long)j * M];
+        const T v = i == j ? make_s<T>(1) : v_col[i];
         const T fv = mul(f, v);
 #pragma unroll
         for (int c = 0; c < CH; ++c)
@@ -110,17 +118,19 @@ __device__ __forceinline__ void apply_reflector(const T* W, int M, int j, T f, T
 // W = 2^-ex A' (A' = A, or A^H when m < n; ex the exponent of max |a_ij|,
 // an exact scaling), then the Householder QR of W: reflectors below the
 // diagonal of W, tau, and R (N x N, ld N, zeros below the diagonal).
-template <class T>
+template <class T, bool SM>
 __global__ void __launch_bounds__(kQrThreads) qr_factor(const QrArgs a) {
     using R = Real<T>;
     constexpr int NT = kQrThreads, NW = NT / 32, CH = kQrChunk;
+    extern __shared__ __align__(16) unsigned char qr_smem[];
     __shared__ T red[NW * CH];
     __shared__ T sh[CH];
     __shared__ R redr[NW];
     const int b = blockIdx.x, tid = threadIdx.x;
     const int M = a.M, N = a.N;
     const T* A = static_cast<const T*>(a.A) + (long long)b * a.sA;
-    T* W = static_cast<T*>(a.W) + (long long)b * M * N;
+    T* const Wg = static_cast<T*>(a.W) + (long long)b * M * N;
+    T* const W = SM ? reinterpret_cast<T*>(qr_smem) : Wg;
     T* tau = static_cast<T*>(a.tau) + (long long)b * N;
     T* Rm = static_cast<T*>(a.R) + (long long)b * N * N;
 
@@ -167,21 +177,26 @@ __global__ void __launch_bounds__(kQrThreads) qr_factor(const QrArgs a) {
         }
         if (!is_zero(tj))
             for (int k0 = j + 1; k0 < N; k0 += CH)
-                apply_reflector(W, M, j, conj_s(tj), W, M, k0, min(CH, N - k0), red, sh);
+                apply_reflector(col, M, j, conj_s(tj), W, M, k0, min(CH, N - k0), red, sh);
         __syncthreads();
     }
     for (int e = tid; e < N * N; e += NT) {
         const int i = e % N, k = e / N;
         Rm[i + (long long)k * N] = i <= k ? W[i + (long long)k * M] : make_s<T>(0);
     }
+    if (SM)   // the reflectors, for qr_apply
+        for (int e = tid; e < M * N; e += NT) Wg[e] = W[e];
     if (tid == 0) a.ex[b] = ex;
 }
 
-// S <- 2^ex S; Y = Q [U_R; 0] (M x N, ld ldy) when Y is wanted.
-template <class T>
+// S <- 2^ex S; Y = Q [U_R; 0] (M x N, ld ldy) when Y is wanted.  SM: Y is
+// built in shared memory (ld M) and written out at the end; each reflector is
+// staged in a shared buffer, the next one read into registers meanwhile.
+template <class T, bool SM>
 __global__ void __launch_bounds__(kQrThreads) qr_apply(const QrArgs a) {
     using R = Real<T>;
-    constexpr int NT = kQrThreads, NW = NT / 32, CH = kQrChunk;
+    constexpr int NT = kQrThreads, NW = NT / 32, CH = kQrChunk, RPT = kQrRowsPerThread;
+    extern __shared__ __align__(16) unsigned char qr_smem[];
     __shared__ T red[NW * CH];
     __shared__ T sh[CH];
     const int b = blockIdx.x, tid = threadIdx.x;
@@ -193,29 +208,89 @@ __global__ void __launch_bounds__(kQrThreads) qr_apply(const QrArgs a) {
     const T* W = static_cast<const T*>(a.W) + (long long)b * M * N;
     const T* tau = static_cast<const T*>(a.tau) + (long long)b * N;
     const T* Uh = static_cast<const T*>(a.Uhat) + (long long)b * N * N;
-    T* Y = static_cast<T*>(a.Y) + (long long)b * a.sY;
-    const int ldy = a.ldy;
+    T* const Yg = static_cast<T*>(a.Y) + (long long)b * a.sY;
+    T* const Y = SM ? reinterpret_cast<T*>(qr_smem) : Yg;
+    const int ldy = SM ? M : a.ldy;
+    T* const vbuf = reinterpret_cast<T*>(qr_smem) + (long long)M * N;    // [2][M], SM only
     for (int e = tid; e < M * N; e += NT) {
         const int i = e % M, k = e / M;
         Y[i + (long long)k * ldy] = i < N ? Uh[i + (long long)k * N] : make_s<T>(0);
     }
+    T nxt[RPT];
+    if (SM) {   // the last reflector into its buffer (buffer j & 1 holds reflector j)
+        T* v0 = vbuf + (long long)((N - 1) & 1) * M;
+#pragma unroll
+        for (int t = 0; t < RPT; ++t) {
+            const int i = N - 1 + tid + t * NT;
+            if (i < M) v0[i] = W[i + (long long)(N - 1) * M];
+        }
+    }
     __syncthreads();
     for (int j = N - 1; j >= 0; --j) {
         const T tj = tau[j];
-        if (is_zero(tj)) continue;
-        for (int k0 = 0; k0 < N; k0 += CH) apply_reflector(W, M, j, tj, Y, ldy, k0, min(CH, N - k0), red, sh);
+        if (SM && j > 0)   // reflector j-1 on its way while j is applied
+#pragma unroll
+            for (int t = 0; t < RPT; ++t) {
+                const int i = j - 1 + tid + t * NT;
+                if (i < M) nxt[t] = W[i + (long long)(j - 1) * M];
+            }
+        const T* v = SM ? vbuf + (long long)(j & 1) * M : W + (long long)j * M;
+        if (!is_zero(tj))
+            for (int k0 = 0; k0 < N; k0 += CH) apply_reflector(v, M, j, tj, Y, ldy, k0, min(CH, N - k0), red, sh);
+        if (SM && j > 0) {
+            T* vn = vbuf + (long long)((j - 1) & 1) * M;
+#pragma unroll
+            for (int t = 0; t < RPT; ++t) {
+                const int i = j - 1 + tid + t * NT;
+                if (i < M) vn[i] = nxt[t];
+            }
+            __syncthreads();
+        }
+    }
+    if (SM) {
+        __syncthreads();
+        for (int e = tid; e < M * N; e += NT) {
+            const int i = e % M, k = e / M;
+            Yg[i + (long long)k * a.ldy] = Y[e];
+        }
     }
 }
 
 template <class T>
+size_t qr_factor_smem(int M, int N) {
+    const size_t b = (size_t)M * N * sizeof(T);
+    return (M <= kQrThreads * kQrRowsPerThread && b <= (size_t)kQrSmemMax) ? b : 0;
+}
+
+template <class T>
+size_t qr_apply_smem(int M, int N) {
+    const size_t b = ((size_t)M * N + 2 * (size_t)M) * sizeof(T);
+    return (M <= kQrThreads * kQrRowsPerThread && b <= (size_t)kQrSmemMax) ? b : 0;
+}
+
+template <class T>
 cudaError_t qr_factor_t(const QrArgs& a, int batch, cudaStream_t st) {
-    qr_factor<T><<<batch, kQrThreads, 0, st>>>(a);
+    const size_t sm = qr_factor_smem<T>(a.M, a.N);
+    if (sm) {
+        const cudaError_t e = allow_dynamic_smem<qr_factor<T, true>>();
+        if (e != cudaSuccess) return e;
+        qr_factor<T, true><<<batch, kQrThreads, sm, st>>>(a);
+    } else {
+        qr_factor<T, false><<<batch, kQrThreads, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t qr_apply_t(const QrArgs& a, int batch, cudaStream_t st) {
-    qr_apply<T><<<batch, kQrThreads, 0, st>>>(a);
+    const size_t sm = a.Y ? qr_apply_smem<T>(a.M, a.N) : 0;
+    if (sm) {
+        const cudaError_t e = allow_dynamic_smem<qr_apply<T, true>>();
+        if (e != cudaSuccess) return e;
+        qr_apply<T, true><<<batch, kQrThreads, sm, st>>>(a);
+    } else {
+        qr_apply<T, false><<<batch, kQrThreads, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
