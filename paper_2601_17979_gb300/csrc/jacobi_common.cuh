@@ -64,31 +64,28 @@ __device__ __forceinline__ double2 warp_sum_s(double2 v) { return make_double2(w
 
 // Rotation tables of the inner solver: two steps' worth (double-buffered, so
 // the next step's rotations can be formed while the current step's are still
-// being applied) of nb disjoint rotations -- c, t = tan(theta), e s with
-// e = e^{i phi}, the index pair and a fired flag -- plus one fired-rotation
-// counter per sweep parity.  Laid out in shared memory right after J.
+// being applied) of nb disjoint rotations, one 16-byte-aligned record per
+// rotation -- c, t = tan(theta), e s with e = e^{i phi}, and the index pair
+// with a fired flag packed in one word -- so a reader fetches a rotation with
+// one or two vector loads; plus one fired-rotation counter per sweep parity.
+// Laid out in shared memory right after J.
 template <class T, int NB>
 struct InnerTables {
     using R = Real<T>;
-    struct Step { R* c; R* t; T* es; int* p; int* q; int* fired; };
-    static constexpr int kStepBytes = NB * ((int)sizeof(T) + 2 * (int)sizeof(R) + 3 * 4);
+    struct alignas(16) Slot {
+        R c, t;
+        T es;
+        int pqf;   // p | q << 8 | fired << 16
+    };
+    using Step = Slot*;
+    static constexpr int kStepBytes = NB * (int)sizeof(Slot);
     char* base;
     int* count;   // [2]
     __device__ explicit InnerTables(void* b)
         : base(static_cast<char*>(b)), count(reinterpret_cast<int*>(static_cast<char*>(b) + 2 * kStepBytes)) {}
-    // Step k's arrays, by address arithmetic (an indexed array of pointer
-    // sets would live in local memory and cost a load per use)
-    __device__ __forceinline__ Step step(int k) const {
-        char* b = base + k * kStepBytes;
-        Step s;
-        s.es = reinterpret_cast<T*>(b);  b += NB * sizeof(T);
-        s.c = reinterpret_cast<R*>(b);   b += NB * sizeof(R);
-        s.t = reinterpret_cast<R*>(b);   b += NB * sizeof(R);
-        s.p = reinterpret_cast<int*>(b); b += NB * sizeof(int);
-        s.q = reinterpret_cast<int*>(b); b += NB * sizeof(int);
-        s.fired = reinterpret_cast<int*>(b);
-        return s;
-    }
+    // step k's records, by address arithmetic (an indexed array of pointers
+    // would live in local memory and cost a load per use)
+    __device__ __forceinline__ Slot* step(int k) const { return reinterpret_cast<Slot*>(base + k * kStepBytes); }
     __host__ __device__ static constexpr int bytes() { return 2 * kStepBytes + 16; }
 };
 
@@ -144,7 +141,7 @@ __device__ __forceinline__ double rotation_tan(double x, double y) {
 // (c, s, e^{i phi}) by Eq. (sin-cos) with sign(0) = +1.  Returns fired.
 template <class T, int NB>
 __device__ __forceinline__ int inner_rotation(const T* G, Real<T> tol, int st, int slot,
-                                              const typename InnerTables<T, NB>::Step& out) {
+                                              typename InnerTables<T, NB>::Slot* out) {
     using R = Real<T>;
     constexpr int TWO = 2 * NB, LDG = TWO + 1;
     int p, q;
@@ -168,8 +165,10 @@ __device__ __forceinline__ int inner_rotation(const T* G, Real<T> tol, int st, i
         c = rsqrt_r(fma_s(t, t, R(1)));
         es = scale(phase_s(gpq, apq), t * c);
     }
-    out.c[slot] = c; out.t[slot] = t; out.es[slot] = es;
-    out.p[slot] = p; out.q[slot] = q; out.fired[slot] = fire;
+    typename InnerTables<T, NB>::Slot rec;
+    rec.c = c; rec.t = t; rec.es = es;
+    rec.pqf = p | (q << 8) | ((fire ? 1 : 0) << 16);
+    out[slot] = rec;
     return fire;
 }
 
@@ -226,11 +225,12 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
                 for (int u = 0; u < NBU; ++u) {
                     f1[u] = f2[u] = 0;
                     if (bq1[u] < 0) continue;
-                    const int q1 = bq1[u], q2 = bq2[u];
-                    f1[u] = cur.fired[q1]; f2[u] = cur.fired[q2];
-                    p1[u] = cur.p[q1]; r1[u] = cur.q[q1]; p2[u] = cur.p[q2]; r2[u] = cur.q[q2];
-                    c1[u] = cur.c[q1]; c2[u] = cur.c[q2]; t1[u] = cur.t[q1];
-                    e1[u] = cur.es[q1]; e2[u] = cur.es[q2];
+                    const auto s1 = cur[bq1[u]], s2 = cur[bq2[u]];
+                    f1[u] = s1.pqf >> 16; f2[u] = s2.pqf >> 16;
+                    p1[u] = s1.pqf & 255; r1[u] = (s1.pqf >> 8) & 255;
+                    p2[u] = s2.pqf & 255; r2[u] = (s2.pqf >> 8) & 255;
+                    c1[u] = s1.c; c2[u] = s2.c; t1[u] = s1.t;
+                    e1[u] = s1.es; e2[u] = s2.es;
                 }
 #pragma unroll
                 for (int u = 0; u < NBU; ++u) {
@@ -300,10 +300,10 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
                     const int e = gt - JW0 + u * JWN;
                     fj[u] = 0;
                     if (e >= TWO * NB) continue;
-                    const int qs = e / TWO;
+                    const auto sj = cur[e / TWO];
                     ij[u] = e % TWO;
-                    fj[u] = cur.fired[qs]; pj[u] = cur.p[qs]; qj[u] = cur.q[qs];
-                    cj[u] = cur.c[qs]; ej[u] = cur.es[qs];
+                    fj[u] = sj.pqf >> 16; pj[u] = sj.pqf & 255; qj[u] = (sj.pqf >> 8) & 255;
+                    cj[u] = sj.c; ej[u] = sj.es;
                 }
 #pragma unroll
                 for (int u = 0; u < NJU; ++u)
