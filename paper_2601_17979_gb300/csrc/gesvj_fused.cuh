@@ -87,12 +87,43 @@ __host__ __device__ inline long long fused_slot_elems(const FusedArgs& a) {
     return w + (long long)a.ldvs * a.Np;
 }
 
-// FP32 adds J^T (2nb x 2nb, 16-byte aligned) for the tiled update.
+// FP32 adds J^T (2nb x 2nb, 16-byte aligned) for the tiled update; the other
+// types a second J (the previous pair's, for the deferred V update).
 template <class T, int NB>
 __host__ __device__ constexpr int fused_group_bytes() {
     return ((2 * (2 * NB) * (2 * NB + 1) * (int)sizeof(T) + InnerTables<T, NB>::bytes() + 15) & ~15) +
-           (std::is_same<T, float>::value ? (2 * NB) * (2 * NB) * 4 : 0);
+           (std::is_same<T, float>::value ? (2 * NB) * (2 * NB) * 4
+                                          : (((2 * NB) * (2 * NB + 1) * (int)sizeof(T) + 15) & ~15));
 }
+
+// The V update of a block pair, [V_i V_j] <- [V_i V_j] J, run by whole warps
+// at a time: a warp takes 32 / 2nb rows, lane c of a row computing output
+// column c (summed over k in order, like the on-chip A update) and writing
+// it after the warp has read the row.  Used to defer a pair's V update into
+// the next pair step's inner sweep, where the FP64 pipe has room.
+template <class T, int NB>
+struct DeferredV {
+    T* V;
+    int ldv, rows;
+    const T* J;        // the pair's J (ld 2nb + 1), or nullptr: nothing pending
+    int bi, bj;
+    __device__ __forceinline__ int tasks() const { return (rows + 32 / (2 * NB) - 1) / (32 / (2 * NB)); }
+    __device__ __forceinline__ void operator()(int wt) const {
+        constexpr int TWO = 2 * NB, LDG = TWO + 1, RPW = 32 / TWO;
+        if (!J || wt >= tasks()) return;                      // uniform over the warp
+        const int lane = threadIdx.x & 31, r = wt * RPW + lane / TWO, c = lane % TWO;
+        T acc = make_s<T>(0);
+        if (r < rows) {
+#pragma unroll
+            for (int k = 0; k < TWO; ++k) {
+                const int ck = k < NB ? bi * NB + k : bj * NB + k - NB;
+                acc = fma_s(V[r + (long long)ck * ldv], J[k + c * LDG], acc);
+            }
+        }
+        __syncwarp();
+        if (r < rows) V[r + (long long)(c < NB ? bi * NB + c : bj * NB + c - NB) * ldv] = acc;
+    }
+};
 
 // Real FP32 keeps two CTAs per SM (its shared memory allows them).
 template <class T>
@@ -116,11 +147,14 @@ __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T
 
     unsigned char* gb = smem + a.offG + g * a.groupBytes;
     T* G = reinterpret_cast<T*>(gb);
-    T* J = G + TWO * LDG;
-    const InnerTables<T, NB> tb(J + TWO * LDG);
-    // J^T for the FP32 tiled update: after the tables, 16-byte aligned
-    float* Jt = reinterpret_cast<float*>(
-        gb + ((2 * TWO * LDG * (int)sizeof(T) + InnerTables<T, NB>::bytes() + 15) & ~15));
+    T* const J0 = G + TWO * LDG;
+    const InnerTables<T, NB> tb(J0 + TWO * LDG);
+    // after the tables, 16-byte aligned: J^T for the FP32 tiled update, or
+    // the second J buffer of the other types
+    unsigned char* const gb_tail = gb + ((2 * TWO * LDG * (int)sizeof(T) + InnerTables<T, NB>::bytes() + 15) & ~15);
+    float* Jt = reinterpret_cast<float*>(gb_tail);
+    T* const J1 = reinterpret_cast<T*>(gb_tail);
+    T* J = J0;
     int* swflag = reinterpret_cast<int*>(smem + a.offMisc);   // [kMaxSweeps] per-sweep "rotated"
     int* iscr = swflag + kMaxSweeps;                           // [4]: 0 bad input, 1 pivot row
     T* bcast = reinterpret_cast<T*>(iscr + 4);                 // [2] broadcast slot
@@ -205,12 +239,20 @@ __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T
     const R tol = (R)a.tol;
     int sw = 0;
     bool converged = false;
+    // FP64 and complex: a pair's V update is deferred to the group's next
+    // pair step and run by the J-update warps during its inner sweep (same
+    // arithmetic; the V blocks are read by nothing else in between)
+    constexpr bool kDefer = !std::is_same<T, float>::value;
+    DeferredV<T, NB> dv{Vs, ldvs, N, nullptr, 0, 0};
     while (sw < a.max_sweeps) {
         for (int r = 0; r < a.L - 1; ++r) {
-            for (int q = g; q < a.L / 2; q += NG) {
+            for (int q0 = 0; q0 < a.L / 2; q0 += NG) {
+              const int q = q0 + g;
+              bool stepped = false;                            // ran an inner sweep this time
+              if (q < a.L / 2) do {
                 int bi, bj;
                 rr_pair(a.L, r, q, bi, bj);
-                if (bj >= a.l) continue;                       // phantom block
+                if (bj >= a.l) break;                          // phantom block
                 auto col = [&](int c) { return c < NB ? bi * NB + c : bj * NB + (c - NB); };
 
                 // S2: G = P^H P, upper triangle, mirrored to keep G Hermitian.
@@ -244,8 +286,21 @@ __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T
                 group_sync(g, GT);
 
                 // S3: inner Jacobi sweeps on G (round-robin over the 2nb indices)
-                const int seen = inner_jacobi<T, NB, GT>(G, J, tb, tol, a.inner_sweeps, gt, g + 1);
-                if (seen == 0) continue;                       // J = I: pair masked (Design-4)
+                int seen;
+                stepped = true;
+                if constexpr (kDefer) {
+                    int ns = 0;
+                    seen = inner_jacobi<T, NB, GT>(G, J, tb, tol, a.inner_sweeps, gt, g + 1, dv, &ns);
+                    if (dv.J) {   // the deferred V rows the background warps did not reach
+                        for (int wt = ns * inner_background_warps<GT>() + (gt >> 5); wt < dv.tasks(); wt += GT / 32)
+                            dv(wt);
+                        dv.J = nullptr;
+                    }
+                    group_sync(g, GT);
+                } else {
+                    seen = inner_jacobi<T, NB, GT>(G, J, tb, tol, a.inner_sweeps, gt, g + 1);
+                }
+                if (seen == 0) break;                       // J = I: pair masked (Design-4)
                 if (gt == 0) swflag[sw] = 1;
 
                 // S4/S5: [W_i W_j] <- [W_i W_j] J and [V_i V_j] <- [V_i V_j] J.
@@ -257,7 +312,7 @@ __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T
                     group_sync(g, GT);
                     update_f32_tiled<NB, GT, 2>(W, ldw, ldw, Vs, ldvs, needVs ? ldvs : 0, bi * NB, bj * NB, Jt, gt, g + 1);
                 } else {
-                    const int rows = M + (needVs ? N : 0);
+                    const int rows = M;                        // V: deferred (DeferredV)
                     const int wg = gt >> 5, half = (gt >> 4) & 1, rl = gt & 15;
                     constexpr int NWG = GT / 32;
                     for (int r0 = wg * 16; r0 < rows; r0 += NWG * 16) {
@@ -285,14 +340,34 @@ __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T
                             for (int c = 0; c < NB; ++c) X[row + col(half * NB + c) * ld] = acc[c];
                         }
                     }
+                    if (needVs) {   // this pair's V update, run during the next pair step
+                        dv.J = J; dv.bi = bi; dv.bj = bj;
+                        J = (J == J0) ? J1 : J0;
+                    }
                 }
                 group_sync(g, GT);
+              } while (0);
+              if (kDefer && !stepped && dv.J) {   // no pair step (phantom or none): apply the pending V update now
+                  for (int wt = gt >> 5; wt < dv.tasks(); wt += GT / 32) dv(wt);
+                  dv.J = nullptr;
+                  group_sync(g, GT);
+              }
+              // FP64 / complex with several pairs per group in a round: the V
+              // updates still deferred from the previous round finish during
+              // each group's first pair step; a barrier after it keeps them
+              // apart from the deferred updates of this round's pairs
+              if (kDefer && q0 == 0 && a.L / 2 > NG) __syncthreads();
             }
             __syncthreads();
         }
         const int fired = swflag[sw];
         ++sw;
         if (!fired) { converged = true; break; }
+    }
+    if constexpr (kDefer) {   // the last pending V update
+        if (dv.J)
+            for (int wt = gt >> 5; wt < dv.tasks(); wt += GT / 32) dv(wt);
+        __syncthreads();
     }
 
     // ---- finalise (Alg. 2): sigma, sort, U = W Sigma^-1, V correction --------

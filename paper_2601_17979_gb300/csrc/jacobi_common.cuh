@@ -184,9 +184,17 @@ __device__ __forceinline__ int inner_rotation(const T* G, Real<T> tol, int st, i
 // gt) sharing named barrier `bar`; the caller must have finished writing G and
 // synchronised.  Returns the number of rotations fired (0: G was diagonal to
 // tol); uniform over the group.
-template <class T, int NB, int GT>
+// Work the caller hands the J-update warps: called once per step by each of
+// them, with a running per-warp task index (step * background warps + warp).
+struct NoBackground {
+    __device__ __forceinline__ void operator()(int) const {}
+};
+template <int GT>
+__host__ __device__ constexpr int inner_background_warps() { return GT > 32 ? GT / 32 - 1 : 1; }
+
+template <class T, int NB, int GT, class Bg = NoBackground>
 __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> tol, int sweeps,
-                            int gt, int bar) {
+                            int gt, int bar, const Bg& bg = Bg(), int* nsteps = nullptr) {
     using R = Real<T>;
     constexpr int TWO = 2 * NB, LDG = TWO + 1, STEPS = TWO - 1;
     constexpr int NBLK = NB * (NB + 1) / 2, NBU = (NBLK + GT - 1) / GT;
@@ -315,8 +323,10 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
                         J[ij[u] + pj[u] * LDG] = rot_add(xj[u], cj[u], yj[u], ces);
                         J[ij[u] + qj[u] * LDG] = rot_sub(yj[u], cj[u], xj[u], es);
                     }
+                bg(gs * inner_background_warps<GT>() + (gt - JW0) / 32);
             }
             named_sync(bar, GT);
+            if (nsteps) *nsteps = gs + 1;
         }
         const int fired = tb.count[isw & 1];
         named_sync(bar, GT);           // all have read it before it is reset
