@@ -134,7 +134,7 @@ constexpr int fused_min_blocks() { return std::is_same<T, float>::value ? 2 : 1;
 // the on-chip kernel, a global-memory slot for the persistent one; the Gram
 // blocks, rotation tables and flags are always in shared memory at the
 // offsets of `a`.  All threads of the CTA call it and return together.
-template <class T, int NB, int NG, int GT>
+template <class T, int NB, int NG, int GT, bool OnChip>
 __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T* const W, T* const Vs,
                                             unsigned char* const smem) {
     using R = Real<T>;
@@ -239,10 +239,12 @@ __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T
     const R tol = (R)a.tol;
     int sw = 0;
     bool converged = false;
-    // FP64 and complex: a pair's V update is deferred to the group's next
-    // pair step and run by the J-update warps during its inner sweep (same
-    // arithmetic; the V blocks are read by nothing else in between)
-    constexpr bool kDefer = !std::is_same<T, float>::value;
+    // FP64 and complex on chip: a pair's V update is deferred to the group's
+    // next pair step and run by the J-update warps during its inner sweep
+    // (same arithmetic; the V blocks are read by nothing else in between).
+    // Not with V in global memory: a warp reads one row of V, which in
+    // global memory would touch a separate cache line per element.
+    constexpr bool kDefer = OnChip && !std::is_same<T, float>::value;
     DeferredV<T, NB> dv{Vs, ldvs, N, nullptr, 0, 0};
     while (sw < a.max_sweeps) {
         for (int r = 0; r < a.L - 1; ++r) {
@@ -312,7 +314,7 @@ __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T
                     group_sync(g, GT);
                     update_f32_tiled<NB, GT, 2>(W, ldw, ldw, Vs, ldvs, needVs ? ldvs : 0, bi * NB, bj * NB, Jt, gt, g + 1);
                 } else {
-                    const int rows = M;                        // V: deferred (DeferredV)
+                    const int rows = M + (needVs && !kDefer ? N : 0);   // on chip V is deferred (DeferredV)
                     const int wg = gt >> 5, half = (gt >> 4) & 1, rl = gt & 15;
                     constexpr int NWG = GT / 32;
                     for (int r0 = wg * 16; r0 < rows; r0 += NWG * 16) {
@@ -340,7 +342,7 @@ __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T
                             for (int c = 0; c < NB; ++c) X[row + col(half * NB + c) * ld] = acc[c];
                         }
                     }
-                    if (needVs) {   // this pair's V update, run during the next pair step
+                    if (kDefer && needVs) {   // this pair's V update, run during the next pair step
                         dv.J = J; dv.bi = bi; dv.bj = bj;
                         J = (J == J0) ? J1 : J0;
                     }
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(NG * GT, fused_min_blocks<T>())
 gesvj_fused_kernel(const FusedArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int mid = a.index ? a.index[blockIdx.x] : (int)blockIdx.x;
-    fused_solve<T, NB, NG, GT>(a, mid, reinterpret_cast<T*>(smem + a.offW), reinterpret_cast<T*>(smem + a.offV),
+    fused_solve<T, NB, NG, GT, true>(a, mid, reinterpret_cast<T*>(smem + a.offW), reinterpret_cast<T*>(smem + a.offV),
                                smem);
 }
 
@@ -448,7 +450,7 @@ gesvj_persistent_kernel(const PersistArgs p) {
         const long long per16 = 16 / (long long)sizeof(T) > 0 ? 16 / (long long)sizeof(T) : 1;
         T* const W = slot;
         T* const Vs = slot + ((long long)a.ldw * a.Np + per16 - 1) / per16 * per16;
-        fused_solve<T, NB, NG, GT>(a, mid, W, Vs, smem);
+        fused_solve<T, NB, NG, GT, false>(a, mid, W, Vs, smem);
         if (p.done) __threadfence_system();                // this thread's outputs before the flag
         __syncthreads();                                   // shared scratch reused next
         if (p.done && threadIdx.x == 0) store_release_sys(p.done + mid, 1);
