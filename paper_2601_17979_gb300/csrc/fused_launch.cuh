@@ -17,6 +17,15 @@ template <> struct FusedCfg<4>  { static constexpr int NG = 2, GT = 32; };
 template <> struct FusedCfg<8>  { static constexpr int NG = 2, GT = 64; };
 template <> struct FusedCfg<16> { static constexpr int NG = 2, GT = 128; };
 
+// A matrix of at most 2nb columns has a single block pair per round, so one
+// of two groups would idle: FP64 and complex then run one group of all the
+// threads (same per-entry arithmetic; FP32's register tiles would sum in
+// another order, so FP32 keeps the two-group shape).
+template <class T>
+__host__ __device__ inline bool fused_single_group(const FusedArgs& a) {
+    return !std::is_same<T, float>::value && a.l == 2;
+}
+
 inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 template <class T, int NB>
@@ -24,6 +33,7 @@ size_t fused_plan_nb(int M, int N, bool needVs, FusedArgs& a, int& nthreads) {
     using C = FusedCfg<NB>;
     using R = Real<T>;
     fused_dims<T, NB>(M, N, a);    // (M, N): the working orientation
+    const int ng = fused_single_group<T>(a) ? 1 : C::NG;
     size_t off = 0;
     a.offW = 0;
     off = align16((size_t)a.ldw * a.Np * sizeof(T));
@@ -31,7 +41,7 @@ size_t fused_plan_nb(int M, int N, bool needVs, FusedArgs& a, int& nthreads) {
     if (needVs) off = align16(off + (size_t)a.ldvs * a.Np * sizeof(T));
     a.offG = (int)off;
     a.groupBytes = fused_group_bytes<T, NB>();
-    off += (size_t)C::NG * a.groupBytes;
+    off += (size_t)ng * a.groupBytes;
     a.offMisc = (int)off;
     const int NT = C::NG * C::GT, NW = NT / 32;
     off += kMaxSweeps * 4 + 16 + 2 * sizeof(T);
@@ -110,6 +120,15 @@ long long persist_slot(int nb, int m, int n) {
 template <class T, int NB>
 cudaError_t fused_launch_nb(const FusedArgs& a, int grid, size_t smem, cudaStream_t st) {
     using C = FusedCfg<NB>;
+    if constexpr (!std::is_same<T, float>::value) {
+        if (fused_single_group<T>(a)) {
+            constexpr auto k1 = gesvj_fused_kernel<T, NB, 1, C::NG * C::GT>;
+            cudaError_t e = allow_dynamic_smem<k1>();
+            if (e != cudaSuccess) return e;
+            k1<<<grid, C::NG * C::GT, smem, st>>>(a);
+            return cudaGetLastError();
+        }
+    }
     constexpr auto k = gesvj_fused_kernel<T, NB, C::NG, C::GT>;
     cudaError_t e = allow_dynamic_smem<k>();
     if (e != cudaSuccess) return e;
