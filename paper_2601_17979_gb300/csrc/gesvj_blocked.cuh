@@ -92,7 +92,10 @@ __global__ void __launch_bounds__(kBlkThreads) blk_gram(const BlockedArgs a, int
     constexpr int KC = (kGramChunk * TWO * (int)sizeof(T) <= 32768) ? kGramChunk
                                                                    : 32768 / (TWO * (int)sizeof(T));
     constexpr int NE = 3 * NB * NB, PER = (NE + NT - 1) / NT;
-    __shared__ T P[KC * TWO];
+    // column stride KC + 1: the threads of a warp read one row of several
+    // columns, which a stride of a multiple of 32 words would put in one bank
+    constexpr int KP = KC + 1;
+    __shared__ T P[KP * TWO];
     const int b = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
     if (blk_skip(a, b)) return;
     int bi, bj;
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__(kBlkThreads) blk_gram(const BlockedArgs a, int
         for (int e = tid; e < KC * TWO; e += NT) {
             const int kk = e % KC, c = e / KC;
             const int col = c < NB ? bi * NB + c : bj * NB + (c - NB);
-            P[kk + c * KC] = kk < kc ? W[k0 + kk + (long long)col * M] : make_s<T>(0);
+            P[kk + c * KP] = kk < kc ? W[k0 + kk + (long long)col * M] : make_s<T>(0);
         }
         __syncthreads();
 #pragma unroll
@@ -123,8 +126,8 @@ __global__ void __launch_bounds__(kBlkThreads) blk_gram(const BlockedArgs a, int
                 const int col = (blk == 2) ? NB + cb : cb;
                 const int split = min(max(mh - k0, 0), kc);    // rows of this chunk below M/2
                 T s0 = lo[u], s1 = hi[u];
-                for (int kk = 0; kk < split; ++kk) s0 = cfma(P[kk + row * KC], P[kk + col * KC], s0);
-                for (int kk = split; kk < kc; ++kk) s1 = cfma(P[kk + row * KC], P[kk + col * KC], s1);
+                for (int kk = 0; kk < split; ++kk) s0 = cfma(P[kk + row * KP], P[kk + col * KP], s0);
+                for (int kk = split; kk < kc; ++kk) s1 = cfma(P[kk + row * KP], P[kk + col * KP], s1);
                 lo[u] = s0;
                 hi[u] = s1;
             }
