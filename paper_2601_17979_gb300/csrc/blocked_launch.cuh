@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <type_traits>
 
 #include "blocked_layout.h"
 #include "gesvj_blocked.cuh"
@@ -54,7 +55,10 @@ cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stag
     // one sweep: every round's stages, then the end-of-sweep bookkeeping
     auto sweep = [&](cudaStream_t s) -> cudaError_t {
         for (int r = 0; r < z.L - 1; ++r) {
-            blk_gram<T, NB><<<gpair, kBlkThreads, 0, s>>>(a, r);
+            if constexpr (std::is_same<T, float>::value && NB >= 8)
+                blk_gram_f32<NB><<<gpair, kBlkThreads, 0, s>>>(a, r);
+            else
+                blk_gram<T, NB><<<gpair, kBlkThreads, 0, s>>>(a, r);
             blk_heevj<T, NB, GT><<<gpair, GT, heevj_smem, s>>>(a, r);
             if (two_stage) {
                 blk_update_stage1<T, NB><<<gupd, kUpdRows, upd_smem, s>>>(a, r);

@@ -31,6 +31,82 @@ __device__ __forceinline__ bool blk_skip(const BlockedArgs& a, int b) {
 }
 
 // ---- load: W = A * 2^-ex (or A^H), padded; V = I; status -------------------
+// ---- S2, real FP32: register tiles --------------------------------------------
+// The full 2nb x 2nb Gram block of the pair in 4 x 4 register tiles (float4
+// reads of row-chunks staged in shared memory, column stride KP = KC + 4: 16-
+// byte aligned, KP/4 odd), each tile's rows split over KS lanes and summed
+// with shuffles at the end; upper tiles written and mirrored.  Twice the
+// flops of the three blocks the generic kernel forms, an eighth of its
+// shared-memory reads per FMA.  Needs KS = 256 / (2nb/4)^2 <= 32: nb >= 8.
+template <int NB>
+__global__ void __launch_bounds__(kBlkThreads) blk_gram_f32(const BlockedArgs a, int r) {
+    constexpr int TWO = 2 * NB, NT = kBlkThreads, TT = TWO / 4, NTILE = TT * TT, KS = NT / NTILE;
+    static_assert(NT % NTILE == 0 && KS >= 1 && KS <= 32 && (KS & (KS - 1)) == 0, "tile split");
+    constexpr int KC = kGramChunk, KP = KC + 4;
+    __shared__ __align__(16) float P[KP * TWO];
+    const int b = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
+    if (blk_skip(a, b)) return;
+    int bi, bj;
+    rr_pair(a.L, r, q, bi, bj);
+    if (bj >= a.l) return;
+    const float* W = static_cast<const float*>(a.W) + b * a.sW;
+    const int M = a.M;
+    const int tile = tid / KS, ks = tid % KS, ti = tile / TT, tj = tile % TT;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int k0 = 0; k0 < M; k0 += KC) {
+        const int kc = min(KC, M - k0);
+        for (int e = tid; e < KC * TWO; e += NT) {
+            const int kk = e % KC, c = e / KC;
+            const int col = c < NB ? bi * NB + c : bj * NB + (c - NB);
+            P[kk + c * KP] = kk < kc ? W[k0 + kk + (long long)col * M] : 0.f;   // zero tail: adds nothing
+        }
+        __syncthreads();
+        const int chunks = (kc + 3) >> 2;
+        for (int ch = ks; ch < chunks; ch += KS) {
+            float4 av[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                av[u] = *reinterpret_cast<const float4*>(P + 4 * ch + (4 * ti + u) * KP);
+                bv[u] = *reinterpret_cast<const float4*>(P + 4 * ch + (4 * tj + u) * KP);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float t = acc[i][j];
+                    t = fmaf(av[i].x, bv[j].x, t);
+                    t = fmaf(av[i].y, bv[j].y, t);
+                    t = fmaf(av[i].z, bv[j].z, t);
+                    t = fmaf(av[i].w, bv[j].w, t);
+                    acc[i][j] = t;
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 1; o < KS; o <<= 1)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += __shfl_xor_sync(0xffffffffu, acc[i][j], o);
+    float* G = static_cast<float*>(a.G) + b * a.sG + (long long)q * TWO * TWO;
+    if (ks == 0 && ti <= tj) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int rr = 4 * ti + i, cc = 4 * tj + j;
+                if (ti == tj && rr > cc) continue;             // diagonal tile: upper part, mirrored
+                G[rr + cc * TWO] = acc[i][j];
+                G[cc + rr * TWO] = acc[i][j];
+            }
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(kBlkThreads) blk_load(const BlockedArgs a) {
     using R = Real<T>;
