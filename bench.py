@@ -772,6 +772,47 @@ def main():
         "clocks": sampler.summary(),
     }
 
+    # end to end through the public API with host buffers: the library's
+    # host-buffer entry point, which copies chunks in and out on its own
+    # streams while other chunks are solved (timed right after the device
+    # step, under the same conditions)
+    if not args.no_e2e:
+        A64p = torch.from_numpy(A64h.transpose(0, 2, 1).copy()).pin_memory().transpose(1, 2)
+        A32p = torch.from_numpy(A32h.transpose(0, 2, 1).copy()).pin_memory().transpose(1, 2)
+
+        def host_outputs(dt, rdt):
+            return (torch.empty((B, N), dtype=rdt).pin_memory(),
+                    torch.empty((B, N, M), dtype=dt).pin_memory().transpose(1, 2),
+                    torch.empty((B, N, N), dtype=dt).pin_memory().transpose(1, 2),
+                    torch.empty(B, dtype=torch.int32).pin_memory(), torch.empty(B, dtype=torch.int32).pin_memory())
+        h64 = host_outputs(torch.float64, torch.float64)
+        h32 = host_outputs(torch.float32, torch.float32)
+        h2d = A64p.numel() * 8 + A32p.numel() * 4
+        d2h = sum(t.numel() * t.element_size() for o in (h64, h32) for t in o)
+        w64 = torch.empty(bsvd.host_workspace_bytes(torch.float64, B, M, N, nb=NB), dtype=torch.uint8, device=dev)
+        w32 = torch.empty(bsvd.host_workspace_bytes(torch.float32, B, M, N, nb=NB), dtype=torch.uint8, device=dev)
+
+        def e2e_step():
+            bsvd.gesvj_host(A64p, nb=NB, tol=TOL_K * U64, out=h64, work=w64, sync=False)
+            bsvd.gesvj_host(A32p, nb=NB, tol=TOL_K * U32, out=h32, work=w32, sync=False)
+        e2e_step()
+        barrier()
+        e_sampler = ClockSampler(gpu_uuid(torch, dev))
+        with e_sampler:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(args.steps):
+                e2e_step()
+            b.record(stream)
+            barrier()
+        e_ms = max_over_ranks(a.elapsed_time(b) / args.steps, dist, dev)
+        ok = bool(torch.equal(h64[0], o64[0].cpu()) and torch.equal(h32[0], o32[0].cpu()))
+        line["e2e"] = {"value": 2 * B * world / (e_ms * 1e-3), "unit": "matrices/s",
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                       "ms_per_step": e_ms, "api": "gesvj_host (bsvd_?gesvj_strided_host)",
+                       "same_sigma_as_device_call": ok, "clocks": e_sampler.summary()}
+        line["gpu_launches"] += 2 * args.steps * 4
+
     # The paper's baseline path on the same FP64 batch ("vs plain FP64 Jacobi"):
     # multi-kernel, inner eigensolver to convergence, two-stage update, no masks.
     variants = [("fp64_mixed", dict(prec="mixed"))] if not args.no_mixed else []
@@ -802,40 +843,6 @@ def main():
                       "info_nonzero": int((o64[3].cpu().numpy() != 0).sum()),
                       "accuracy_worst_over_bound": acc}
         del work
-
-    # end to end through the public API with host buffers
-    if not args.no_e2e:
-        A64p = torch.from_numpy(A64h.transpose(0, 2, 1).copy()).pin_memory()
-        A32p = torch.from_numpy(A32h.transpose(0, 2, 1).copy()).pin_memory()
-        host_out = [tuple(torch.empty(t.shape, dtype=t.dtype).pin_memory() if t.dim() < 3 else
-                          torch.empty((t.shape[0], t.shape[2], t.shape[1]), dtype=t.dtype).pin_memory()
-                          for t in o) for o in (o64, o32)]
-        d64 = torch.empty((B, N, M), dtype=torch.float64, device=dev)
-        d32 = torch.empty((B, N, M), dtype=torch.float32, device=dev)
-        h2d = A64p.numel() * 8 + A32p.numel() * 4
-        d2h = sum(t.numel() * t.element_size() for o in (o64, o32) for t in o)
-
-        def e2e_step():
-            d64.copy_(A64p, non_blocking=True)
-            d32.copy_(A32p, non_blocking=True)
-            bsvd.gesvj(d64.transpose(1, 2), nb=NB, tol=TOL_K * U64, out=o64)
-            bsvd.gesvj(d32.transpose(1, 2), nb=NB, tol=TOL_K * U32, out=o32)
-            for o, ho in zip((o64, o32), host_out):
-                for t, h in zip(o, ho):
-                    h.copy_(t if t.dim() < 3 else t.transpose(1, 2), non_blocking=True)
-        e2e_step()
-        barrier()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
-        b.record(stream)
-        barrier()
-        e_ms = max_over_ranks(a.elapsed_time(b) / args.steps, dist, dev)
-        line["e2e"] = {"value": 2 * B * world / (e_ms * 1e-3), "unit": "matrices/s",
-                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                       "ms_per_step": e_ms}
-        line["gpu_launches"] += 2 * args.steps
 
     # CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -160,6 +160,36 @@ bsvd_status bsvd_cgesvj_strided(BSVD_STRIDED_ARGS(void, float));    /* T = compl
 bsvd_status bsvd_zgesvj_strided(BSVD_STRIDED_ARGS(void, double));   /* T = complex double */
 
 /*
+ * Strided batch with HOST buffers (the paper has no counterpart; for callers
+ * whose matrices live in host memory).  Same arguments as the strided call,
+ * with A, S, U, V, info and sweeps in host memory -- page-locked
+ * (cudaHostAlloc / cudaHostRegister) for the copies to overlap, pageable
+ * works but each copy then waits -- and d_work a device workspace of
+ * bsvd_gesvj_host_workspace() bytes (256-byte aligned).  The batch is cut
+ * into up to four chunks of at least 4 x SMs matrices: chunk c+1 is copied in
+ * and chunk c-1's results copied out while chunk c is solved, on two
+ * handle-owned copy streams, and alternate chunks are solved on `stream` and
+ * a second handle-owned stream so one chunk's last wave overlaps the next
+ * chunk's first.  Returns after enqueueing; the host outputs are complete
+ * once `stream` reaches the end of the call.  Do not touch the host buffers
+ * before then.  Argument positions as for the strided call (host pointers in
+ * place of device ones); opts as for the strided call.
+ */
+#define BSVD_STRIDED_HOST_ARGS(T, R)                                                        \
+    bsvd_handle handle, bsvd_job jobu, bsvd_job jobv, int batch, int m, int n,               \
+    const T* hA, int lda, long long strideA, R* hS, long long strideS,                       \
+    T* hU, int ldu, long long strideU, T* hV, int ldv, long long strideV,                    \
+    int* h_info, int* h_sweeps, void* d_work, size_t work_bytes, const bsvd_opts* opts,      \
+    void* stream
+
+bsvd_status bsvd_gesvj_host_workspace(bsvd_handle handle, char dtype, int batch, int m, int n,
+                                      bsvd_job jobu, bsvd_job jobv, const bsvd_opts* opts, size_t* bytes);
+bsvd_status bsvd_sgesvj_strided_host(BSVD_STRIDED_HOST_ARGS(float, float));
+bsvd_status bsvd_dgesvj_strided_host(BSVD_STRIDED_HOST_ARGS(double, double));
+bsvd_status bsvd_cgesvj_strided_host(BSVD_STRIDED_HOST_ARGS(void, float));
+bsvd_status bsvd_zgesvj_strided_host(BSVD_STRIDED_HOST_ARGS(void, double));
+
+/*
  * Autotuner (the paper's "decision layer" of Sec. 4.2 picks a GEMM kernel from
  * an offline table; here the whole configuration is timed online).  Times the
  * candidates -- block width nb in {4, 8, 16, 32} x {on-chip fused path,

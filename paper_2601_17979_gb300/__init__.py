@@ -11,12 +11,13 @@ masking, as hand-written CUDA kernels behind the C-ABI of include/bsvd.h.
     res.S, res.U, res.V, res.info, res.sweeps
 """
 from .buildlib import build
-from .binding import (BsvdError, SVDResult, Server, gesvj, gesvj_batched, autotune, load, handle, make_opts,
+from .binding import (BsvdError, SVDResult, Server, gesvj, gesvj_host, host_workspace_bytes, gesvj_batched,
+                      autotune, load, handle, make_opts,
                       column_major, empty_column_major, workspace_bytes, EXPORTS,
                       FLAG_NO_V_CORRECTION, FLAG_TWO_STAGE, FLAG_NO_MASKS, FLAG_NO_GRAPH,
                       FLAG_SYNC_CHECK, FLAG_QR)
 
-__all__ = ["build", "BsvdError", "SVDResult", "Server", "gesvj", "gesvj_batched", "autotune", "load", "handle",
+__all__ = ["build", "BsvdError", "SVDResult", "Server", "gesvj", "gesvj_host", "host_workspace_bytes", "gesvj_batched", "autotune", "load", "handle",
            "make_opts", "column_major", "empty_column_major", "workspace_bytes", "EXPORTS",
            "FLAG_NO_V_CORRECTION", "FLAG_TWO_STAGE", "FLAG_NO_MASKS", "FLAG_NO_GRAPH",
            "FLAG_SYNC_CHECK", "FLAG_QR"]

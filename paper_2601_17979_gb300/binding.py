@@ -36,6 +36,8 @@ EXPORTS = (
     "bsvd_sgesvj_strided", "bsvd_dgesvj_strided", "bsvd_cgesvj_strided", "bsvd_zgesvj_strided",
     "bsvd_sgesvj_batched", "bsvd_dgesvj_batched", "bsvd_cgesvj_batched", "bsvd_zgesvj_batched",
     "bsvd_dgesvj_strided_noalloc", "bsvd_autotune_workspace", "bsvd_autotune",
+    "bsvd_gesvj_host_workspace", "bsvd_sgesvj_strided_host", "bsvd_dgesvj_strided_host",
+    "bsvd_cgesvj_strided_host", "bsvd_zgesvj_strided_host",
     "bsvd_server_clock", "bsvd_server_create", "bsvd_server_submit", "bsvd_server_replay",
     "bsvd_server_test", "bsvd_server_wait", "bsvd_server_result", "bsvd_server_fetch",
     "bsvd_server_release", "bsvd_server_collect", "bsvd_server_cancel", "bsvd_server_pause",
@@ -97,6 +99,12 @@ def load() -> ctypes.CDLL:
                     P, I, I, I, P, P, P, P, P, P, P, P, P, P, P, P, SZ, ctypes.POINTER(Opts), P]
             L.bsvd_autotune_workspace.argtypes = [P, ctypes.c_char, I, I, I, I, I, ctypes.POINTER(Opts),
                                                   ctypes.POINTER(SZ)]
+            L.bsvd_gesvj_host_workspace.argtypes = [P, ctypes.c_char, I, I, I, I, I, ctypes.POINTER(Opts),
+                                                    ctypes.POINTER(SZ)]
+            for t in "sdcz":
+                getattr(L, f"bsvd_{t}gesvj_strided_host").argtypes = [
+                    P, I, I, I, I, I, P, I, LL, P, LL, P, I, LL, P, I, LL, P, P, P, SZ,
+                    ctypes.POINTER(Opts), P]
             L.bsvd_autotune.argtypes = [P, ctypes.c_char, I, I, I, I, I, P, I, LL, P, SZ,
                                         ctypes.POINTER(Opts), ctypes.POINTER(Opts), P, P]
             D = ctypes.c_double
@@ -243,6 +251,71 @@ def gesvj(A: torch.Tensor, compute_u: bool = True, compute_v: bool = True, *, nb
     if squeeze:
         return SVDResult(S[0], U[0] if U is not None else None, V[0] if V is not None else None,
                          info, sweeps)
+    return SVDResult(S, U, V, info, sweeps)
+
+
+def host_workspace_bytes(dtype, batch: int, m: int, n: int, compute_u=True, compute_v=True, **opts) -> int:
+    """Device workspace (bytes) of ``gesvj_host`` for a (batch, m, n) batch."""
+    L, h = load(), handle()
+    o = make_opts(**opts)
+    nbytes = ctypes.c_size_t()
+    t = DTYPES[dtype] if not isinstance(dtype, str) else dtype
+    _check(L.bsvd_gesvj_host_workspace(h, t.encode(), batch, m, n, int(compute_u), int(compute_v),
+                                       ctypes.byref(o), ctypes.byref(nbytes)), "bsvd_gesvj_host_workspace")
+    return max(int(nbytes.value), 256)
+
+
+def gesvj_host(A: torch.Tensor, compute_u: bool = True, compute_v: bool = True, *, nb: int = 0,
+               tol: float = 0.0, max_sweeps: int = 0, inner_sweeps: int = 0, path="auto", flags: int = 0,
+               prec="native", out=None, work=None, stream=None, sync: bool = True) -> SVDResult:
+    """SVD of a batch in HOST memory (batch, m, n), through the library's
+    chunked copy / compute pipeline (``bsvd_?gesvj_strided_host``).
+
+    A is read column-major (a page-locked copy is made if it is pageable or
+    not column-major); the results are page-locked CPU tensors in the layout of
+    ``gesvj`` (``out`` may pass them preallocated, page-locked).  With
+    sync=False the call returns once the work is queued on `stream`.
+    """
+    if A.dtype not in DTYPES:
+        raise TypeError(f"unsupported dtype {A.dtype}")
+    if A.is_cuda:
+        raise ValueError("gesvj_host takes a CPU tensor; use gesvj for device memory")
+    if A.dim() == 2:
+        A = A.unsqueeze(0)
+    A = column_major(A)
+    if not A.is_pinned():
+        A = A.transpose(1, 2).contiguous().pin_memory().transpose(1, 2)
+    batch, m, n = A.shape
+    k = min(m, n)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if out is None:
+        S = torch.empty((batch, k), dtype=REAL[A.dtype]).pin_memory()
+        U = torch.empty((batch, k, m), dtype=A.dtype).pin_memory().transpose(1, 2) if compute_u else None
+        V = torch.empty((batch, k, n), dtype=A.dtype).pin_memory().transpose(1, 2) if compute_v else None
+        info = torch.empty(batch, dtype=torch.int32).pin_memory()
+        sweeps = torch.empty(batch, dtype=torch.int32).pin_memory()
+    else:
+        S, U, V, info, sweeps = out
+    o = make_opts(nb, tol, max_sweeps, inner_sweeps, path, flags, prec)
+    t = DTYPES[A.dtype]
+    L, h = load(), handle()
+    if work is None:
+        nbytes = ctypes.c_size_t()
+        _check(L.bsvd_gesvj_host_workspace(h, t.encode(), batch, m, n, int(compute_u), int(compute_v),
+                                           ctypes.byref(o), ctypes.byref(nbytes)), "bsvd_gesvj_host_workspace")
+        work = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=dev)
+    st = getattr(L, f"bsvd_{t}gesvj_strided_host")(
+        h, int(compute_u), int(compute_v), batch, m, n, A.data_ptr(), leading_dim(A), A.stride(0),
+        S.data_ptr(), S.stride(0) if batch > 1 else k,
+        U.data_ptr() if U is not None else None, leading_dim(U) if U is not None else 1,
+        U.stride(0) if U is not None else 0,
+        V.data_ptr() if V is not None else None, leading_dim(V) if V is not None else 1,
+        V.stride(0) if V is not None else 0,
+        info.data_ptr(), sweeps.data_ptr() if sweeps is not None else None,
+        work.data_ptr(), work.numel(), ctypes.byref(o), _stream_ptr(stream))
+    _check(st, f"bsvd_{t}gesvj_strided_host")
+    if sync:
+        (stream or torch.cuda.current_stream()).synchronize()
     return SVDResult(S, U, V, info, sweeps)
 
 

@@ -37,6 +37,8 @@ struct bsvd_handle_s {
     std::map<bsvd_tune_key, bsvd_tuned> tuned;
     cudaStream_t cap = nullptr;   // private stream on which sweeps are recorded into CUDA graphs
     int cap_device = -1;
+    cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};   // host-buffer pipeline: H2D, D2H, 2nd compute
+    int pipe_device = -1;
 };
 
 namespace {
@@ -841,6 +843,9 @@ bsvd_status bsvd_create(bsvd_handle* handle) {
 
 bsvd_status bsvd_destroy(bsvd_handle handle) {
     if (handle && handle->cap) cudaStreamDestroy(handle->cap);
+    if (handle)
+        for (cudaStream_t s : handle->pipe)
+            if (s) cudaStreamDestroy(s);
     delete handle;
     return BSVD_OK;
 }
@@ -1020,6 +1025,196 @@ bsvd_status bsvd_autotune(bsvd_handle handle, char dtype, bsvd_job jobu, bsvd_jo
     return BSVD_OK;
 }
 
+namespace {
+
+// ---- strided batch with host buffers: a chunked copy / compute pipeline -------
+struct HostPlan {
+    int chunk = 0, nchunks = 0;
+    size_t off[7];        // A, S, U, V, info, sweeps, solver workspace (one buffer set)
+    size_t set_bytes = 0, bytes = 0;
+};
+
+bsvd_status plan_host(bsvd_handle h, char t, int batch, int m, int n, bool wantU, bool wantV, const bsvd_opts* opts,
+                      HostPlan& hp) {
+    const TypeOps ops = ops_for(t);
+    const size_t e = ops.elt, re_ = ops.single ? 4 : 8;
+    const int k = std::min(m, n);
+    // 4 chunks of at least 4 waves of CTAs each; alternate chunks run on two
+    // compute streams so one chunk's tail overlaps the next chunk's start
+    const int minc = 4 * device_sms_or_default(h);
+    hp.chunk = std::max(1, std::min(batch, std::max(minc, (batch + 3) / 4)));
+    hp.nchunks = (batch + hp.chunk - 1) / hp.chunk;
+    int mm[1] = {m}, nn[1] = {n};
+    size_t ws = 0;
+    bsvd_status st = bsvd_gesvj_workspace(h, t, hp.chunk, mm, nn, 1, wantU ? BSVD_JOB_SOME : BSVD_JOB_NONE,
+                                          wantV ? BSVD_JOB_SOME : BSVD_JOB_NONE, opts, &ws);
+    if (st != BSVD_OK) return st;
+    const size_t c = (size_t)hp.chunk;
+    const size_t sizes[7] = {c * m * n * e, c * k * re_, wantU ? c * m * k * e : 0, wantV ? c * n * k * e : 0,
+                             c * sizeof(int), c * sizeof(int), ws};
+    size_t pos = 0;
+    for (int i = 0; i < 7; ++i) { hp.off[i] = pos; pos += align256(std::max<size_t>(sizes[i], 1)); }
+    hp.set_bytes = pos;
+    hp.bytes = (hp.nchunks > 1 ? 2 : 1) * pos;
+    return BSVD_OK;
+}
+
+cudaError_t pipe_streams(bsvd_handle h) {
+    if (h->pipe[0] && h->pipe_device == h->device) return cudaSuccess;
+    for (cudaStream_t& s : h->pipe) {
+        if (s) cudaStreamDestroy(s);
+        s = nullptr;
+    }
+    for (cudaStream_t& s : h->pipe) {
+        const cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    h->pipe_device = h->device;
+    return cudaSuccess;
+}
+
+// Copy of `count` matrices rows x cols (column pitch ld, matrix stride sd,
+// element e bytes) between host and device layouts.
+cudaError_t copy_mats(void* dst, size_t dld, long long dsd, const void* src, size_t sld, long long ssd, int rows,
+                      int cols, int count, size_t e, cudaMemcpyKind kind, cudaStream_t s) {
+    if (rows == 0 || cols == 0 || count == 0) return cudaSuccess;
+    if (dsd == (long long)dld * cols && ssd == (long long)sld * cols)   // one pitched copy of count * cols columns
+        return cudaMemcpy2DAsync(dst, dld * e, src, sld * e, rows * e, (size_t)cols * count, kind, s);
+    for (int i = 0; i < count; ++i) {
+        const cudaError_t err = cudaMemcpy2DAsync(static_cast<char*>(dst) + (size_t)i * dsd * e, dld * e,
+                                                  static_cast<const char*>(src) + (size_t)i * ssd * e, sld * e,
+                                                  rows * e, cols, kind, s);
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
+bsvd_status host_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, int batch, int m, int n, const void* hA,
+                      int lda, long long sA, void* hS, long long sS, void* hU, int ldu, long long sU, void* hV,
+                      int ldv, long long sV, int* h_info, int* h_sweeps, void* d_work, size_t work_bytes,
+                      const bsvd_opts* opts, void* stream) {
+    if (!h) return BSVD_ERR_INVALID;
+    h->last_arg = 0;
+    const int k = std::min(m, n);
+    if (jobu != BSVD_JOB_NONE && jobu != BSVD_JOB_SOME) return fail_arg(h, 2);
+    if (jobv != BSVD_JOB_NONE && jobv != BSVD_JOB_SOME) return fail_arg(h, 3);
+    if (batch < 0) return fail_arg(h, 4);
+    if (m < 0) return fail_arg(h, 5);
+    if (n < 0) return fail_arg(h, 6);
+    const bool wantU = jobu == BSVD_JOB_SOME, wantV = jobv == BSVD_JOB_SOME;
+    if (batch > 0 && m > 0 && n > 0 && !hA) return fail_arg(h, 7);
+    if (lda < std::max(1, m)) return fail_arg(h, 8);
+    if (batch > 1 && sA < (long long)lda * n) return fail_arg(h, 9);
+    if (batch > 0 && k > 0 && !hS) return fail_arg(h, 10);
+    if (batch > 1 && sS < k) return fail_arg(h, 11);
+    if (wantU && batch > 0 && k > 0 && !hU) return fail_arg(h, 12);
+    if (wantU && ldu < std::max(1, m)) return fail_arg(h, 13);
+    if (wantU && batch > 1 && sU < (long long)ldu * k) return fail_arg(h, 14);
+    if (wantV && batch > 0 && k > 0 && !hV) return fail_arg(h, 15);
+    if (wantV && ldv < std::max(1, n)) return fail_arg(h, 16);
+    if (wantV && batch > 1 && sV < (long long)ldv * k) return fail_arg(h, 17);
+    if (batch > 0 && !h_info) return fail_arg(h, 18);
+    if (d_work && (reinterpret_cast<uintptr_t>(d_work) & 255) != 0) return fail_arg(h, 20);
+    Resolved r;
+    if (!resolve(opts, ops_for(t).single, k, r)) return fail_arg(h, 22);
+    if (batch == 0 || k == 0) return BSVD_OK;
+    if (batch == 1) {   // strides are not used: make them the packed ones
+        sA = (long long)lda * n; sS = k; sU = (long long)ldu * k; sV = (long long)ldv * k;
+    }
+    bsvd_status st = refresh_device(h);
+    if (st != BSVD_OK) return st;
+    HostPlan hp;
+    st = plan_host(h, t, batch, m, n, wantU, wantV, opts, hp);
+    if (st != BSVD_OK) return st;
+    if (!d_work || work_bytes < hp.bytes) return BSVD_ERR_WORKSPACE;
+    cudaError_t e = pipe_streams(h);
+    if (e != cudaSuccess) return fail_cuda(h, e);
+    const TypeOps ops = ops_for(t);
+    const size_t el = ops.elt, rel = ops.single ? 4 : 8;
+    cudaStream_t s0 = static_cast<cudaStream_t>(stream), h2d = h->pipe[0], d2h = h->pipe[1], s1 = h->pipe[2];
+    const int C = hp.nchunks;
+    std::vector<cudaEvent_t> ev_h2d(C), ev_comp(C), ev_d2h(C);
+    cudaEvent_t start = nullptr;
+    auto cleanup = [&]() {
+        for (int c = 0; c < C; ++c) {
+            if (ev_h2d[c]) cudaEventDestroy(ev_h2d[c]);
+            if (ev_comp[c]) cudaEventDestroy(ev_comp[c]);
+            if (ev_d2h[c]) cudaEventDestroy(ev_d2h[c]);
+        }
+        if (start) cudaEventDestroy(start);
+    };
+    auto ck = [&](cudaError_t err) { if (err != cudaSuccess && e == cudaSuccess) e = err; return err == cudaSuccess; };
+    ck(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    for (int c = 0; c < C && e == cudaSuccess; ++c) {
+        ck(cudaEventCreateWithFlags(&ev_h2d[c], cudaEventDisableTiming));
+        ck(cudaEventCreateWithFlags(&ev_comp[c], cudaEventDisableTiming));
+        ck(cudaEventCreateWithFlags(&ev_d2h[c], cudaEventDisableTiming));
+    }
+    // the pipeline's streams start after what the caller queued on `stream`
+    if (e == cudaSuccess && ck(cudaEventRecord(start, s0)))
+        for (cudaStream_t x : {h2d, d2h, s1}) ck(cudaStreamWaitEvent(x, start, 0));
+    char* w = static_cast<char*>(d_work);
+    auto set = [&](int c) { return w + (size_t)(c & 1) * hp.set_bytes; };
+    auto rows_of = [&](int c) { return std::min(hp.chunk, batch - c * hp.chunk); };
+    auto h2d_chunk = [&](int c) {
+        if (c >= 2) ck(cudaStreamWaitEvent(h2d, ev_comp[c - 2], 0));          // the buffer's A is free
+        const long long i0 = (long long)c * hp.chunk;
+        ck(copy_mats(set(c) + hp.off[0], m, (long long)m * n, static_cast<const char*>(hA) + i0 * sA * el, lda, sA,
+                     m, n, rows_of(c), el, cudaMemcpyHostToDevice, h2d));
+        ck(cudaEventRecord(ev_h2d[c], h2d));
+    };
+    auto compute_chunk = [&](int c) -> bsvd_status {
+        cudaStream_t cs = (c & 1) ? s1 : s0;
+        ck(cudaStreamWaitEvent(cs, ev_h2d[c], 0));
+        if (c >= 2) ck(cudaStreamWaitEvent(cs, ev_d2h[c - 2], 0));             // the buffer's outputs are read out
+        if (e != cudaSuccess) return BSVD_ERR_CUDA;
+        char* b = set(c);
+        const bsvd_status rs = strided_impl(t, h, jobu, jobv, rows_of(c), m, n, b + hp.off[0], std::max(1, m),
+                                            (long long)m * n, b + hp.off[1], k, b + hp.off[2], std::max(1, m),
+                                            (long long)m * k, b + hp.off[3], std::max(1, n), (long long)n * k,
+                                            reinterpret_cast<int*>(b + hp.off[4]), reinterpret_cast<int*>(b + hp.off[5]),
+                                            b + hp.off[6], hp.set_bytes - hp.off[6], opts, cs);
+        if (rs != BSVD_OK) return rs;
+        ck(cudaEventRecord(ev_comp[c], cs));
+        return BSVD_OK;
+    };
+    auto d2h_chunk = [&](int c) {
+        ck(cudaStreamWaitEvent(d2h, ev_comp[c], 0));
+        const long long i0 = (long long)c * hp.chunk;
+        const int cnt = rows_of(c);
+        char* b = set(c);
+        ck(copy_mats(static_cast<char*>(hS) + i0 * sS * rel, sS, sS, b + hp.off[1], k, k, k, 1, cnt, rel,
+                     cudaMemcpyDeviceToHost, d2h));
+        if (wantU) ck(copy_mats(static_cast<char*>(hU) + i0 * sU * el, ldu, sU, b + hp.off[2], m, (long long)m * k,
+                                m, k, cnt, el, cudaMemcpyDeviceToHost, d2h));
+        if (wantV) ck(copy_mats(static_cast<char*>(hV) + i0 * sV * el, ldv, sV, b + hp.off[3], n, (long long)n * k,
+                                n, k, cnt, el, cudaMemcpyDeviceToHost, d2h));
+        ck(cudaMemcpyAsync(h_info + i0, b + hp.off[4], cnt * sizeof(int), cudaMemcpyDeviceToHost, d2h));
+        if (h_sweeps) ck(cudaMemcpyAsync(h_sweeps + i0, b + hp.off[5], cnt * sizeof(int), cudaMemcpyDeviceToHost, d2h));
+        ck(cudaEventRecord(ev_d2h[c], d2h));
+    };
+    bsvd_status rs = BSVD_OK;
+    for (int c = 0; c < std::min(C, 2) && e == cudaSuccess && rs == BSVD_OK; ++c) {
+        h2d_chunk(c);
+        rs = compute_chunk(c);
+    }
+    for (int c = 0; c < C && e == cudaSuccess && rs == BSVD_OK; ++c) {
+        d2h_chunk(c);
+        if (c + 2 < C) {
+            h2d_chunk(c + 2);
+            rs = compute_chunk(c + 2);
+        }
+    }
+    // `stream` reaches the end of the call after every copy out
+    if (e == cudaSuccess && rs == BSVD_OK)
+        for (int c = std::max(0, C - 2); c < C; ++c) ck(cudaStreamWaitEvent(s0, ev_d2h[c], 0));
+    cleanup();
+    if (rs != BSVD_OK) return rs;
+    return e == cudaSuccess ? BSVD_OK : fail_cuda(h, e);
+}
+
+}  // namespace
+
 #define BSVD_STRIDED_IMPL(TAG, T, R)                                                          \
     bsvd_status bsvd_##TAG##gesvj_strided(BSVD_STRIDED_ARGS(T, R)) {                           \
         return strided_impl(#TAG[0], handle, jobu, jobv, batch, m, n, dA, lda, strideA, dS,    \
@@ -1030,6 +1225,35 @@ BSVD_STRIDED_IMPL(s, float, float)
 BSVD_STRIDED_IMPL(d, double, double)
 BSVD_STRIDED_IMPL(c, void, float)
 BSVD_STRIDED_IMPL(z, void, double)
+
+bsvd_status bsvd_gesvj_host_workspace(bsvd_handle handle, char dtype, int batch, int m, int n, bsvd_job jobu,
+                                      bsvd_job jobv, const bsvd_opts* opts, size_t* bytes) {
+    if (!handle) return BSVD_ERR_INVALID;
+    handle->last_arg = 0;
+    if (dtype != 's' && dtype != 'd' && dtype != 'c' && dtype != 'z') return fail_arg(handle, 2);
+    if (batch < 0) return fail_arg(handle, 3);
+    if (m < 0) return fail_arg(handle, 4);
+    if (n < 0) return fail_arg(handle, 5);
+    if (!bytes) return fail_arg(handle, 9);
+    *bytes = 0;
+    if (batch == 0 || std::min(m, n) == 0) return BSVD_OK;
+    HostPlan hp;
+    const bsvd_status st = plan_host(handle, dtype, batch, m, n, jobu == BSVD_JOB_SOME, jobv == BSVD_JOB_SOME,
+                                     opts, hp);
+    if (st == BSVD_OK) *bytes = hp.bytes;
+    return st;
+}
+
+#define BSVD_HOST_IMPL(TAG, T, R)                                                              \
+    bsvd_status bsvd_##TAG##gesvj_strided_host(BSVD_STRIDED_HOST_ARGS(T, R)) {                  \
+        return host_impl(#TAG[0], handle, jobu, jobv, batch, m, n, hA, lda, strideA, hS,        \
+                         strideS, hU, ldu, strideU, hV, ldv, strideV, h_info, h_sweeps,         \
+                         d_work, work_bytes, opts, stream);                                     \
+    }
+BSVD_HOST_IMPL(s, float, float)
+BSVD_HOST_IMPL(d, double, double)
+BSVD_HOST_IMPL(c, void, float)
+BSVD_HOST_IMPL(z, void, double)
 
 #define BSVD_BATCHED_IMPL(TAG, T, R)                                                          \
     bsvd_status bsvd_##TAG##gesvj_batched(BSVD_BATCHED_ARGS(T, R)) {                           \
