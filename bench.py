@@ -617,6 +617,54 @@ def run_mixed96(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_square(args, rank, world, local):
+    """Square batches with entries U[0,1] (the paper's larnv inputs), n from
+    64 to 512: matrices/s and algorithmic TFLOP/s per type and size; matrices
+    up to ~100 columns run on chip, larger ones on the multi-kernel path."""
+    import torch
+    import paper_2601_17979_gb300 as bsvd
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    bsvd.build()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)    # larger than L2
+    stream = torch.cuda.current_stream(dev)
+    sizes = args.sizes or [64, 128, 256, 512]
+    rows = []
+    for t, dt in (("d", torch.float64), ("s", torch.float32)):
+        for n in sizes:
+            B = args.batch if args.batch != BATCH else {64: 2000, 128: 1000, 256: 200, 512: 50}.get(n, 32)
+            rng = synth.rng_for(synth.SEED_BASE + 7, n * 2 + (t == "s"))
+            A = torch.from_numpy(rng.uniform(0, 1, (B, n, n))).to(dt).to(dev).transpose(1, 2)
+            res = bsvd.gesvj(A)                                            # warm-up
+            times = []
+            for _ in range(max(1, args.steps)):
+                flush.fill_(1)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                res = bsvd.gesvj(A)
+                b.record(stream)
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+            ms = statistics.median(times)
+            sw = res.sweeps.cpu().numpy()
+            nb = 16 if n >= 48 else (8 if n >= 12 else 4)
+            f = matrix_flops(n, n, nb, sw)
+            rows.append({"dtype": t, "n": n, "batch": B, "ms": ms, "matrices_per_s": B / (ms * 1e-3),
+                         "tflops": f / (ms * 1e-3) / 1e12, "sweeps_mean": float(sw.mean()),
+                         "info_nonzero": int((res.info != 0).sum().item())})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    head = max(rows, key=lambda r: (r["dtype"] == "d", r["n"]))
+    line = {"metric": f"batch SVD matrices/s (square {head['n']}x{head['n']} FP64, U[0,1])",
+            "value": head["matrices_per_s"], "unit": "matrices/s", "n_gpus": world, "steps": args.steps,
+            "warmup": 1, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "square: n x n, entries U[0,1], FP64 and FP32, U, Sigma, V; median of steps",
+                       "l2": "L2 flushed (256 MB write) before every timed call"},
+            "results": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def config_dict(world, per_rank):
     return {"workload": "tall128x64: 10,000 FP64 (sigma geometric 1..1e-6) + 10,000 FP32 "
                         "(1..1e-3) matrices 128x64 = Q1 diag(sigma) Q2^T, Haar Q1, Q2",
@@ -639,12 +687,14 @@ def main():
     ap.add_argument("--ladder", action="store_true", help="also time Design-2/3/4 (multi-kernel)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision FP64 leg")
     ap.add_argument("--workload", default="tall128x64",
-                    choices=["tall128x64", "uneven", "serving", "tallskinny", "mixed96"],
+                    choices=["tall128x64", "uneven", "serving", "tallskinny", "mixed96", "square"],
                     help="tall128x64 (default); uneven: 10,000 FP32 + 10,000 complex64 matrices, "
                          "m ~ U{8..512}, n ~ U{8..m}, one persistent launch per type; serving: a Poisson "
                          "stream of single-matrix requests at the continuous-batching server; tallskinny: "
                          "n = 16, m = 100..2000, with and without QR pre-processing; mixed96: the clustered "
-                         "96x96 FP64/complex128 set, mixed precision against native FP64")
+                         "96x96 FP64/complex128 set, mixed precision against native FP64; square: n x n "
+                         "U[0,1] batches, n = 64..512")
+    ap.add_argument("--sizes", type=int, nargs="*", default=None, help="square: the sizes n")
     ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (default 50,000)")
     ap.add_argument("--seconds", type=float, default=0.0, help="serving: stream length (default 10 s)")
     ap.add_argument("--drain", type=float, default=10.0, help="serving: seconds to drain after arrivals")
@@ -672,6 +722,9 @@ def main():
         return
     if args.workload == "mixed96":
         run_mixed96(args, rank, world, local)
+        return
+    if args.workload == "square":
+        run_square(args, rank, world, local)
         return
 
     import torch

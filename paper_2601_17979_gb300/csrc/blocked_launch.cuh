@@ -115,6 +115,12 @@ cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stag
         if (e != cudaSuccess) return e;
     }
     blk_finalize<T><<<a.count, kBlkThreads, fin_smem, st>>>(a);
+    if (a.trans ? a.wantU : a.wantV) {
+        const int nt = (a.N + kFinBT - 1) / kFinBT;
+        const dim3 gfin(a.count, nt, nt);
+        if (!(a.flags & 1)) blk_fin_gram<T><<<gfin, kFinThreads, 0, st>>>(a);
+        blk_fin_z<T><<<gfin, kFinThreads, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -15,7 +15,7 @@ struct BlockedArgs {
     int count;                 // matrices in this launch group
     // workspace, per matrix: W (M x Np, ld M), Vw (N x Np, ld N), G and J
     // (L/2 blocks of 2nb x 2nb), T (L/2 x (M+N) x 2nb two-stage temporary,
-    // also the finalisation scratch: >= N*N + M elements)
+    // also the finalisation scratch: >= M + N*N + N elements)
     void* W; void* Vw; void* G; void* J; void* T;
     long long sW, sVw, sG, sJ, sT;
     int* state;                // count x 4: status (1 active, 0 converged, -1 bad), rotated, sweeps, exponent
@@ -53,7 +53,7 @@ inline BlkSizes blk_sizes(int nb, int M, int N, bool two_stage) {
     z.V = (long long)N * z.Np;
     z.G = pairs * two * two;
     z.J = z.G;
-    const long long fin = (long long)M + (long long)N * N;           // finalisation scratch
+    const long long fin = (long long)M + (long long)N * N + N;       // finalisation: x, E, rank
     z.T = std::max(two_stage ? pairs * (M + N) * two : 0LL, fin);
     return z;
 }

@@ -379,6 +379,13 @@ static __global__ void blk_converge(const BlockedArgs a) {
 }
 
 // ---- a7: finalise -------------------------------------------------------------
+// rank of each column of a finished matrix, kept in the finalisation scratch
+// after x (M) and E (N x N)
+template <class T>
+__device__ __forceinline__ int* fin_rank(const BlockedArgs& a, int b) {
+    return reinterpret_cast<int*>(static_cast<T*>(a.T) + b * a.sT + a.M + (long long)a.N * a.N);
+}
+
 template <class T>
 __global__ void __launch_bounds__(kBlkThreads) blk_finalize(const BlockedArgs a) {
     using R = Real<T>;
@@ -417,18 +424,148 @@ __global__ void __launch_bounds__(kBlkThreads) blk_finalize(const BlockedArgs a)
     }
     const T* W = static_cast<const T*>(a.W) + b * a.sW;
     const T* V = static_cast<const T*>(a.Vw) + b * a.sVw;
-    T* scratch = static_cast<T*>(a.T) + b * a.sT;        // x (M), then E (N x N)
-    const bool needVs = a.trans ? a.wantU : a.wantV;
+    T* scratch = static_cast<T*>(a.T) + b * a.sT;        // x (M), E (N x N), rank (N)
     const bool wantWout = a.trans ? a.wantV : a.wantU;
     T* Y = a.trans ? Vout : Uout;
-    T* Z = a.trans ? Uout : Vout;
     const FinalScratch<T> fs{sig, rank, red, iscr, bcast};
+    // Sigma and U here; V (and its Newton-Schulz step) in the tiled kernels
+    // below, which read the columns' ranks from the workspace
     finalize_outputs<T, NT>(W, M, V, N, M, N, ex, scratch, scratch + M, N,
-                            !(a.flags & 1), Sout, Y, a.trans ? ldv : ldu, wantWout, Z,
-                            a.trans ? ldu : ldv, needVs, fs);
+                            false, Sout, Y, a.trans ? ldv : ldu, wantWout, nullptr, 1, false, fs);
+    int* grank = fin_rank<T>(a, b);
+    for (int k = tid; k < N; k += NT) grank[k] = rank[k];
     if (tid == 0) {
         a.info[mid] = status == 0 ? 0 : sw;
         if (a.sweeps) a.sweeps[mid] = sw;
+    }
+}
+
+// ---- Newton-Schulz step of V over the whole GPU ------------------------------
+// The correction of the end of Alg. 2 costs 1.5 N^3 multiply-adds per matrix,
+// more than the rest of the finalisation together once N is in the hundreds,
+// so it runs as two tiled products over (matrix, 64 x 64 output tile) CTAs:
+//   blk_fin_gram: E = V^H V - I (upper tiles, mirrored);
+//   blk_fin_z:    Z[:, rank_k] = v_k - (V E)_k / 2 (a plain copy without the step).
+// Each output keeps one accumulator over the contraction index in increasing
+// order: the rounding sequence of the on-chip finalisation.
+enum : int { kFinBT = 64, kFinKC = 16, kFinThreads = 256 };
+
+template <class T, bool ConjA>
+__device__ __forceinline__ void fin_mac(T (&acc)[4][4], const T (*As)[kFinBT + 1], const T (*Bs)[kFinBT + 1],
+                                        int tr, int tc, int kmax) {
+    auto step = [&](int kk) {
+        T x[4], y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { x[u] = As[kk][tr + 16 * u]; y[u] = Bs[kk][tc + 16 * u]; }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = ConjA ? cfma(x[u], y[v], acc[u][v]) : fma_s(x[u], y[v], acc[u][v]);
+    };
+    if (kmax == kFinKC) {
+#pragma unroll
+        for (int kk = 0; kk < kFinKC; ++kk) step(kk);
+    } else {
+        for (int kk = 0; kk < kmax; ++kk) step(kk);
+    }
+}
+
+template <class T>
+__device__ __forceinline__ bool fin_skip(const BlockedArgs& a, int b) {
+    return a.state[4 * b] < 0 || !(a.trans ? a.wantU : a.wantV);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kFinThreads) blk_fin_gram(const BlockedArgs a) {
+    using R = Real<T>;
+    const int b = blockIdx.x, ta = blockIdx.y, tb = blockIdx.z, tid = threadIdx.x;
+    if (ta > tb || fin_skip<T>(a, b)) return;
+    __shared__ T As[kFinKC][kFinBT + 1], Bs[kFinKC][kFinBT + 1];
+    const int N = a.N, r0 = ta * kFinBT, c0 = tb * kFinBT, tr = tid & 15, tc = tid >> 4;
+    const T* V = static_cast<const T*>(a.Vw) + b * a.sVw;                // N x N, ld N
+    T* E = static_cast<T*>(a.T) + b * a.sT + a.M;                         // N x N, ld N
+    const T zero = make_s<T>(0);
+    T acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = zero;
+    for (int i0 = 0; i0 < N; i0 += kFinKC) {
+        for (int e = tid; e < kFinKC * kFinBT; e += kFinThreads) {
+            const int kk = e % kFinKC, cc = e / kFinKC, i = i0 + kk;
+            As[kk][cc] = (i < N && r0 + cc < N) ? V[i + (long long)(r0 + cc) * N] : zero;
+            Bs[kk][cc] = (i < N && c0 + cc < N) ? V[i + (long long)(c0 + cc) * N] : zero;
+        }
+        __syncthreads();
+        fin_mac<T, true>(acc, As, Bs, tr, tc, min(kFinKC, N - i0));
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int r = r0 + tr + 16 * u, c = c0 + tc + 16 * v;
+            if (r >= N || c >= N || r > c) continue;
+            T x = acc[u][v];
+            if (r == c) x = make_s<T>(re(x) - R(1));
+            E[r + (long long)c * N] = x;
+            E[c + (long long)r * N] = conj_s(x);
+        }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kFinThreads) blk_fin_z(const BlockedArgs a) {
+    using R = Real<T>;
+    const int b = blockIdx.x, ti = blockIdx.y, tk = blockIdx.z, tid = threadIdx.x;
+    if (fin_skip<T>(a, b)) return;
+    __shared__ T As[kFinKC][kFinBT + 1], Bs[kFinKC][kFinBT + 1];
+    const int N = a.N, r0 = ti * kFinBT, c0 = tk * kFinBT, tr = tid & 15, tc = tid >> 4;
+    const bool correct = !(a.flags & 1);
+    const T* V = static_cast<const T*>(a.Vw) + b * a.sVw;
+    const T* E = static_cast<const T*>(a.T) + b * a.sT + a.M;
+    const int* rank = fin_rank<T>(a, b);
+    const int mid = blk_mid(a, b);
+    T* Z;
+    long long ldz;
+    if (a.trans) {
+        Z = a.Up ? static_cast<T*>(a.Up[mid]) : static_cast<T*>(a.U) + (long long)mid * a.sU;
+        ldz = a.ldup ? a.ldup[mid] : a.ldu;
+    } else {
+        Z = a.Vp ? static_cast<T*>(a.Vp[mid]) : static_cast<T*>(a.V) + (long long)mid * a.sV;
+        ldz = a.ldvp ? a.ldvp[mid] : a.ldv;
+    }
+    const T zero = make_s<T>(0);
+    T acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = zero;
+    if (correct) {
+        for (int j0 = 0; j0 < N; j0 += kFinKC) {
+            for (int e = tid; e < kFinKC * kFinBT; e += kFinThreads) {
+                const int rr = e % kFinBT, ka = e / kFinBT;
+                As[ka][rr] = (j0 + ka < N && r0 + rr < N) ? V[(r0 + rr) + (long long)(j0 + ka) * N] : zero;
+                const int kb = e % kFinKC, cc = e / kFinKC;
+                Bs[kb][cc] = (j0 + kb < N && c0 + cc < N) ? E[(j0 + kb) + (long long)(c0 + cc) * N] : zero;
+            }
+            __syncthreads();
+            fin_mac<T, false>(acc, As, Bs, tr, tc, min(kFinKC, N - j0));
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const int k = c0 + tc + 16 * v;
+        if (k >= N) continue;
+        T* zc = Z + (long long)rank[k] * ldz;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = r0 + tr + 16 * u;
+            if (i >= N) continue;
+            T z = V[i + (long long)k * N];
+            if (correct) z = sub(z, scale(acc[u][v], R(0.5)));
+            zc[i] = z;
+        }
     }
 }
 

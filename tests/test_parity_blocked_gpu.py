@@ -75,6 +75,20 @@ def test_blocked_equals_fused_bitwise_fp64():
     assert np.array_equal(S1, S2) and np.array_equal(U1, U2) and np.array_equal(V1, V2)
 
 
+@pytest.mark.parametrize("m,n,flags", [(100, 72, 0), (72, 100, 0), (100, 72, bsvd.FLAG_NO_V_CORRECTION)])
+def test_blocked_equals_fused_bitwise_fp64_tiled_finalisation(m, n, flags):
+    """The multi-kernel path forms V's Newton-Schulz step in 64 x 64 output
+    tiles; with k = 72 that is two tiles and a ragged tail per side, and the
+    bits still match the on-chip finalisation (one accumulator per output,
+    contraction index in increasing order).  m < n puts the step on U."""
+    rng = np.random.default_rng(m * n + flags)
+    mats = [rng.standard_normal((m, n)) for _ in range(4)]
+    S1, U1, V1, i1, w1 = run_gpu(mats, nb=8, path="fused", flags=flags)
+    S2, U2, V2, i2, w2 = run_gpu(mats, nb=8, path="blocked", flags=flags)
+    assert (i1 == 0).all() and np.array_equal(w1, w2)
+    assert np.array_equal(S1, S2) and np.array_equal(U1, U2) and np.array_equal(V1, V2)
+
+
 def test_blocked_and_fused_agree_fp32():
     """FP32: the on-chip kernel sums its register-tiled Gram in another order,
     so the two paths agree to the bounds, not bitwise."""
@@ -90,7 +104,7 @@ def test_blocked_and_fused_agree_fp32():
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32, np.complex128, np.complex64])
 @pytest.mark.parametrize("m,n,nb", [(200, 150, 16), (150, 260, 16), (257, 33, 8), (130, 130, 32),
-                                    (64, 64, 32), (300, 5, 4)])
+                                    (64, 64, 32), (300, 5, 4), (140, 136, 16)])
 def test_large_shapes_blocked(dtype, m, n, nb):
     rng = np.random.default_rng(m + n + nb)
     if np.issubdtype(dtype, np.complexfloating):
