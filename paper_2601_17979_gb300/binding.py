@@ -13,6 +13,7 @@ import os
 import threading
 from collections import namedtuple
 
+import numpy as np
 import torch
 
 from . import buildlib as _build
@@ -319,11 +320,31 @@ def gesvj_host(A: torch.Tensor, compute_u: bool = True, compute_v: bool = True, 
     return SVDResult(S, U, V, info, sweeps)
 
 
+def _flat_outputs(sizes, dtype, device):
+    """One allocation for a list of outputs of `sizes` elements each, every
+    output starting on a 256-byte boundary (as separate allocations would).
+    Returns the flat tensor, the element offsets and the device pointers."""
+    elt = torch.empty((), dtype=dtype).element_size()
+    step = max(1, 256 // elt)
+    sizes = np.asarray(sizes, dtype=np.int64)
+    padded = (sizes + step - 1) // step * step
+    off = np.zeros(len(sizes), dtype=np.int64)
+    if len(sizes) > 1:
+        np.cumsum(padded[:-1], out=off[1:])
+    flat = torch.empty(max(int(padded.sum()), 1), dtype=dtype, device=device)
+    ptr = torch.from_numpy(flat.data_ptr() + off * elt).to(device, non_blocking=False)
+    return flat, off, ptr
+
+
 def gesvj_batched(mats, compute_u: bool = True, compute_v: bool = True, *, nb: int = 0,
                   tol: float = 0.0, max_sweeps: int = 0, inner_sweeps: int = 0, path="auto",
                   flags: int = 0, stream=None):
     """SVD of a list of CUDA matrices of any shapes (one dtype) through the
-    pointer-array entry point.  Returns lists S, U, V and info, sweeps."""
+    pointer-array entry point.  Returns lists S, U, V and info, sweeps.
+
+    The outputs of all matrices share one allocation per array (views into
+    it); the call returns once the work is queued on the stream, like any
+    torch operation."""
     mats = [column_major(x) if x.dim() == 2 else None for x in mats]
     if any(x is None for x in mats):
         raise ValueError("every matrix must be 2-D")
@@ -332,21 +353,23 @@ def gesvj_batched(mats, compute_u: bool = True, compute_v: bool = True, *, nb: i
         raise TypeError("all matrices must share one supported dtype")
     dev = mats[0].device
     B = len(mats)
-    ms = (ctypes.c_int * max(B, 1))(*[x.shape[0] for x in mats])
-    ns = (ctypes.c_int * max(B, 1))(*[x.shape[1] for x in mats])
-    lda = (ctypes.c_int * max(B, 1))(*[leading_dim(x) for x in mats])
-    S = [torch.empty(min(x.shape), dtype=REAL[dt], device=dev) for x in mats]
-    U = [torch.empty((min(x.shape), x.shape[0]), dtype=dt, device=dev).t() for x in mats] if compute_u else None
-    V = [torch.empty((min(x.shape), x.shape[1]), dtype=dt, device=dev).t() for x in mats] if compute_v else None
-    ldu = (ctypes.c_int * max(B, 1))(*[max(x.shape[0], 1) for x in mats])
-    ldv = (ctypes.c_int * max(B, 1))(*[max(x.shape[1], 1) for x in mats])
+    m_np = np.fromiter((x.shape[0] for x in mats), dtype=np.int64, count=B)
+    n_np = np.fromiter((x.shape[1] for x in mats), dtype=np.int64, count=B)
+    k_np = np.minimum(m_np, n_np)
+    lda_np = np.fromiter((leading_dim(x) for x in mats), dtype=np.int64, count=B)
 
-    def ptrs(ts):
-        return torch.tensor([t.data_ptr() for t in ts], dtype=torch.int64, device=dev)
+    def cints(v):
+        return (ctypes.c_int * max(B, 1))(*v.tolist())
 
-    pA, pS = ptrs(mats), ptrs(S)
-    pU = ptrs(U) if U is not None else None
-    pV = ptrs(V) if V is not None else None
+    ms, ns, lda = cints(m_np), cints(n_np), cints(lda_np)
+    ldu, ldv = cints(np.maximum(m_np, 1)), cints(np.maximum(n_np, 1))
+    pA = torch.from_numpy(np.fromiter((x.data_ptr() for x in mats), dtype=np.int64, count=B)).to(dev)
+    Sf, offS, pS = _flat_outputs(k_np, REAL[dt], dev)
+    Uf = Vf = pU = pV = None
+    if compute_u:
+        Uf, offU, pU = _flat_outputs(m_np * k_np, dt, dev)
+    if compute_v:
+        Vf, offV, pV = _flat_outputs(n_np * k_np, dt, dev)
     info = torch.empty(B, dtype=torch.int32, device=dev)
     sweeps = torch.empty(B, dtype=torch.int32, device=dev)
     o = make_opts(nb, tol, max_sweeps, inner_sweeps, path, flags)
@@ -366,8 +389,18 @@ def gesvj_batched(mats, compute_u: bool = True, compute_v: bool = True, *, nb: i
            ctypes.cast(ldv, ctypes.c_void_p), info.data_ptr(), sweeps.data_ptr(),
            work.data_ptr(), work.numel(), ctypes.byref(o), _stream_ptr(stream))
     _check(st, f"bsvd_{t}gesvj_batched")
-    # keep the pointer arrays and workspace alive until the kernels finish
-    torch.cuda.current_stream(dev).synchronize() if stream is None else stream.synchronize()
+    if stream is not None:
+        # the temporaries return to torch's allocator when this call returns:
+        # tie their reuse to the stream the kernels run on
+        for x in [pA, pS, pU, pV, work, Sf, Uf, Vf, info, sweeps] + mats:
+            if x is not None:
+                x.record_stream(stream)
+    # views into the flat outputs, formed while the GPU works
+    S = [Sf.narrow(0, int(o_), int(k)) for o_, k in zip(offS, k_np)]
+    U = [Uf.narrow(0, int(o_), int(m * k)).view(int(k), int(m)).t() for o_, m, k in zip(offU, m_np, k_np)] \
+        if compute_u else None
+    V = [Vf.narrow(0, int(o_), int(n * k)).view(int(k), int(n)).t() for o_, n, k in zip(offV, n_np, k_np)] \
+        if compute_v else None
     return SVDResult(S, U, V, info, sweeps)
 
 

@@ -263,6 +263,56 @@ __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T
                 // FP32: register-tiled (fused_f32.cuh).
                 if constexpr (std::is_same<T, float>::value) {
                     gram_f32_tiled<NB, GT>(W, ldw, M, bi * NB, bj * NB, G, gt);
+                } else if constexpr (!OnChip) {
+                    // W in global memory: 2 x 2 tiles of upper entries per lane
+                    // pair, four independent sums (half the loads per FMA of
+                    // one entry at a time); each entry still sums k in order
+                    // over its half of the rows, so the bits are those of the
+                    // branch below
+                    constexpr int TH = TWO / 2, NTL = TH * (TH + 1) / 2, NWG = GT / 32;
+                    const int wg = gt >> 5, kh = (gt >> 4) & 1, el = gt & 15;
+                    const int kb = kh ? M / 2 : 0, ke = kh ? M : M / 2;
+                    for (int t0 = wg * 16; t0 < NTL; t0 += NWG * 16) {
+                        const int t = t0 + el;
+                        int ti = 0, tj = 0;
+                        T acc[2][2];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u)
+#pragma unroll
+                            for (int v = 0; v < 2; ++v) acc[u][v] = make_s<T>(0);
+                        if (t < NTL) {
+                            tri_index(t, ti, tj);
+                            const T* x0 = W + col(2 * ti) * ldw;
+                            const T* x1 = W + col(2 * ti + 1) * ldw;
+                            const T* y0 = W + col(2 * tj) * ldw;
+                            const T* y1 = W + col(2 * tj + 1) * ldw;
+#pragma unroll 4
+                            for (int k = kb; k < ke; ++k) {
+                                const T a0 = x0[k], a1 = x1[k], b0 = y0[k], b1 = y1[k];
+                                acc[0][0] = cfma(a0, b0, acc[0][0]);
+                                acc[0][1] = cfma(a0, b1, acc[0][1]);
+                                acc[1][0] = cfma(a1, b0, acc[1][0]);
+                                acc[1][1] = cfma(a1, b1, acc[1][1]);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < 2; ++u)
+#pragma unroll
+                            for (int v = 0; v < 2; ++v) acc[u][v] = add(acc[u][v], shfl_xor_s(acc[u][v], 16));
+                        if (kh == 0 && t < NTL) {
+#pragma unroll
+                            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                                for (int v = 0; v < 2; ++v) {
+                                    const int ca = 2 * ti + u, cb = 2 * tj + v;
+                                    if (ca > cb) continue;             // lower entry of a diagonal tile
+                                    T x = acc[u][v];
+                                    if (ca == cb) x = make_s<T>(re(x));
+                                    G[ca + cb * LDG] = x;
+                                    G[cb + ca * LDG] = conj_s(x);
+                                }
+                        }
+                    }
                 } else {
                     constexpr int NUP = TWO * (TWO + 1) / 2, NWG = GT / 32;
                     const int wg = gt >> 5, kh = (gt >> 4) & 1, el = gt & 15;

@@ -165,3 +165,20 @@ def test_qr_workspace_query(L):
         binding.workspace_bytes("d", [(1000, 16), (900, 16)], False, flags=binding.FLAG_QR)
     with pytest.raises(binding.BsvdError, match="NOT_IMPLEMENTED"):
         binding.workspace_bytes("d", [(1000, 16)], True, batch=2, flags=binding.FLAG_QR, prec="mixed")
+
+
+def test_flat_outputs_layout():
+    """The pointer-array binding puts every matrix's output in one allocation:
+    each output starts 256 bytes after a boundary of the previous one's end,
+    pointers match the views, and empty outputs take no room."""
+    import numpy as np
+    import torch
+    from paper_2601_17979_gb300.binding import _flat_outputs
+    m = np.array([5, 0, 7, 3, 64]); k = np.minimum(m, np.array([3, 4, 7, 1, 64]))
+    for dt in (torch.float32, torch.complex128):
+        flat, off, ptr = _flat_outputs(m * k, dt, "cpu")
+        elt = flat.element_size()
+        assert ((off * elt) % 256 == 0).all()
+        ends = off + m * k
+        assert (ends[:-1] <= off[1:]).all() and ends[-1] <= flat.numel()
+        assert (ptr.numpy() - flat.data_ptr() == off * elt).all()
