@@ -236,7 +236,10 @@ def run_uneven(args, rank, world, local):
     groups = {}
     for x in mats:
         groups.setdefault(x.dtype, []).append(x)
-    dev_mats = {dt: [torch.from_numpy(x).to(dev) for x in lst] for dt, lst in groups.items()}
+    # resident in the library's column-major layout (a row-major view would
+    # make the binding copy every matrix on every call)
+    dev_mats = {dt: [torch.from_numpy(np.asfortranarray(x)).to(dev) for x in lst] for dt, lst in groups.items()}
+    assert all(t.stride(0) == 1 for lst in dev_mats.values() for t in lst if t.shape[1] > 1)
     stream = torch.cuda.current_stream(dev)
 
     def barrier():
@@ -289,7 +292,7 @@ def run_uneven(args, rank, world, local):
     # runs one launch -- or one multi-kernel sweep loop -- per matrix)
     sub = {}
     for x in mats[:min(B, 500)]:
-        sub.setdefault(x.dtype, []).append(torch.from_numpy(x).to(dev))
+        sub.setdefault(x.dtype, []).append(torch.from_numpy(np.asfortranarray(x)).to(dev))
     barrier()
     a.record(stream)
     for dt, T in sub.items():

@@ -587,7 +587,9 @@ bsvd_status plan_persistent(int sms, const TypeOps& ops, int batch, const int* m
     if (!fused_nb(pp.nb)) return BSVD_ERR_NOT_IMPLEMENTED;
     pp.slot = 0;
     for (int id : pp.order) pp.slot = std::max(pp.slot, ops.slot(pp.nb, m[id], n[id]));
-    pp.grid = std::max(1, std::min(pp.count, sms * (ops.single ? 2 : 1)));
+    // resident CTAs per SM of the persistent kernel: two (register cap 128)
+    // except for complex128
+    pp.grid = std::max(1, std::min(pp.count, sms * (ops.elt == 16 ? 1 : 2)));
     pp.ints = align256((size_t)(6 * (size_t)batch + 1) * sizeof(int));
     pp.bytes = pp.ints + align256((size_t)pp.grid * pp.slot * ops.elt);
     return BSVD_OK;

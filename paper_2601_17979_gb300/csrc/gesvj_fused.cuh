@@ -476,8 +476,16 @@ __device__ __forceinline__ void store_release_sys(int* p, int v) {
     asm volatile("st.release.sys.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Two CTAs per SM for every type but complex128: with W in global memory the
+// kernel is latency-bound, and a second CTA's groups hide more of it than
+// the registers the cap (128) takes away.
+template <class T>
+constexpr int persist_min_blocks() {
+    return std::is_same<T, double2>::value ? 1 : 2;
+}
+
 template <class T, int NB, int NG, int GT>
-__global__ void __launch_bounds__(NG * GT, fused_min_blocks<T>())
+__global__ void __launch_bounds__(NG * GT, persist_min_blocks<T>())
 gesvj_persistent_kernel(const PersistArgs p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_mid;
