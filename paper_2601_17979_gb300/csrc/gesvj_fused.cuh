@@ -363,6 +363,58 @@ __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T
                     for (int e = gt; e < TWO * TWO; e += GT) Jt[(e / TWO) + (e % TWO) * TWO] = J[(e % TWO) + (e / TWO) * LDG];
                     group_sync(g, GT);
                     update_f32_tiled<NB, GT, 2>(W, ldw, ldw, Vs, ldvs, needVs ? ldvs : 0, bi * NB, bj * NB, Jt, gt, g + 1);
+                } else if constexpr (std::is_same<T, float2>::value) {
+                    // complex64: 4 rows x 2nb/8 columns per lane (columns
+                    // cg, cg + 8, ...: conflict-free J reads with its padded
+                    // stride), a 16-row slab per warp; each output still sums
+                    // k in order, the bits of the generic branch below.  The
+                    // generic mapping (one row, nb columns per lane) reads J
+                    // once per multiply-add, two-way bank-conflicted, and is
+                    // bound by shared-memory wavefronts in single precision.
+                    constexpr int CJ = TWO / 8, NWG = GT / 32;
+                    const int rows = M + (needVs && !kDefer ? N : 0);
+                    const int wg = gt >> 5, cg = gt & 7, rs = (gt >> 3) & 3;
+                    for (int r0 = wg * 16; r0 < rows; r0 += NWG * 16) {
+                        T* X[4];
+                        int ldx[4];
+                        bool ok[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int r = r0 + rs + 4 * i;
+                            ok[i] = r < rows;
+                            X[i] = r < M ? W + r : Vs + (r - M);
+                            ldx[i] = r < M ? ldw : ldvs;
+                        }
+                        T acc[4][CJ];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int j = 0; j < CJ; ++j) acc[i][j] = make_s<T>(0);
+#pragma unroll 4
+                        for (int k = 0; k < TWO; ++k) {
+                            const int ck = col(k);
+                            T xk[4], jk[CJ];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) xk[i] = ok[i] ? X[i][ck * ldx[i]] : make_s<T>(0);
+#pragma unroll
+                            for (int j = 0; j < CJ; ++j) jk[j] = J[k + (cg + 8 * j) * LDG];
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                                for (int j = 0; j < CJ; ++j) acc[i][j] = fma_s(xk[i], jk[j], acc[i][j]);
+                        }
+                        __syncwarp();
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            if (ok[i]) {
+#pragma unroll
+                                for (int j = 0; j < CJ; ++j) X[i][col(cg + 8 * j) * ldx[i]] = acc[i][j];
+                            }
+                    }
+                    if (kDefer && needVs) {   // this pair's V update, run during the next pair step
+                        dv.J = J; dv.bi = bi; dv.bj = bj;
+                        J = (J == J0) ? J1 : J0;
+                    }
                 } else {
                     const int rows = M + (needVs && !kDefer ? N : 0);   // on chip V is deferred (DeferredV)
                     const int wg = gt >> 5, half = (gt >> 4) & 1, rl = gt & 15;
