@@ -25,6 +25,7 @@ STATUS = {0: "BSVD_OK", -1: "BSVD_ERR_INVALID", -2: "BSVD_ERR_WORKSPACE", -3: "B
 PATHS = {"auto": 0, "fused": 1, "plain": 2, "blocked": 3, "persistent": 4}
 PATH_NAMES = {v: k for k, v in PATHS.items()}
 FLAG_NO_V_CORRECTION, FLAG_TWO_STAGE, FLAG_NO_MASKS, FLAG_NO_GRAPH, FLAG_SYNC_CHECK, FLAG_QR = 1, 2, 4, 8, 16, 32
+FLAG_SPLIT_LARGE = 64
 DTYPES = {torch.float32: "s", torch.float64: "d", torch.complex64: "c", torch.complex128: "z"}
 REAL = {torch.float32: torch.float32, torch.float64: torch.float64,
         torch.complex64: torch.float32, torch.complex128: torch.float64}
@@ -68,7 +69,7 @@ class Opts(ctypes.Structure):
 
 _lock = threading.Lock()
 _lib = None
-_handle = None
+_handles = threading.local()
 
 
 def lib_path() -> str:
@@ -129,16 +130,18 @@ def load() -> ctypes.CDLL:
 
 
 def handle() -> ctypes.c_void_p:
-    global _handle
-    L = load()
-    with _lock:
-        if _handle is None:
-            h = ctypes.c_void_p()
-            st = L.bsvd_create(ctypes.byref(h))
-            if st != BSVD_OK:
-                raise BsvdError(st, "bsvd_create")
-            _handle = h
-    return _handle
+    """This thread's library handle (a handle is not thread-safe, so each
+    host thread gets its own; autotuned choices live in the handle that
+    recorded them)."""
+    h = getattr(_handles, "h", None)
+    if h is None:
+        L = load()
+        h = ctypes.c_void_p()
+        st = L.bsvd_create(ctypes.byref(h))
+        if st != BSVD_OK:
+            raise BsvdError(st, "bsvd_create")
+        _handles.h = h
+    return h
 
 
 def _check(st: int, where: str):

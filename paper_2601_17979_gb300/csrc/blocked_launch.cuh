@@ -18,26 +18,49 @@ template <> struct BlkCfg<8>  { static constexpr int GT = 64; };
 template <> struct BlkCfg<16> { static constexpr int GT = 128; };
 template <> struct BlkCfg<32> { static constexpr int GT = 256; };
 
+// `var` (nullptr for a batch of one shape) gives a variable-shape batch: each
+// matrix's shape and workspace offsets, and the maxima that size the grids;
+// a smaller matrix's CTAs return at once in the rounds, pairs and rows it
+// does not have.
 template <class T, int NB>
 cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stage, bool host_sync,
-                       cudaStream_t capture) {
+                       cudaStream_t capture, const BlkVarPlan* var) {
     using R = Real<T>;
     constexpr int TWO = 2 * NB, GT = BlkCfg<NB>::GT, LDG = TWO + 1;
-    const BlkSizes z = blk_sizes(NB, a.M, a.N, two_stage);
-    a.l = z.l; a.L = z.L; a.Np = z.Np;
-    a.sW = z.W; a.sVw = z.V; a.sG = z.G; a.sJ = z.J; a.sT = z.T;
+    cudaError_t e;
+    long long nW, nV, nG, nJ;                  // region sizes, elements
+    if (!var) {
+        const BlkSizes z = blk_sizes(NB, a.M, a.N, two_stage);
+        a.l = z.l; a.L = z.L; a.Np = z.Np;
+        a.sW = z.W; a.sVw = z.V; a.sG = z.G; a.sJ = z.J; a.sT = z.T;
+        nW = a.count * z.W; nV = a.count * z.V; nG = a.count * z.G; nJ = a.count * z.J;
+        a.shapes = nullptr;
+    } else {
+        if (two_stage || (int)var->shapes.size() != a.count) return cudaErrorInvalidValue;
+        a.M = var->Mmax; a.N = var->Nmax; a.l = var->lmax; a.L = var->Lmax; a.Np = var->lmax * NB;
+        a.sW = a.sVw = a.sG = a.sJ = a.sT = 0;
+        nW = var->W; nV = var->V; nG = var->G; nJ = var->J;
+    }
     char* p = static_cast<char*>(work);
     a.state = reinterpret_cast<int*>(p);       p += blk_align((size_t)a.count * 4 * sizeof(int));
-    a.pairflag = reinterpret_cast<int*>(p);    p += blk_align((size_t)a.count * (z.L / 2) * sizeof(int));
+    a.pairflag = reinterpret_cast<int*>(p);    p += blk_align((size_t)a.count * (a.L / 2) * sizeof(int));
     a.any_active = reinterpret_cast<int*>(p);  p += blk_align(sizeof(int));
+    if (var) {
+        BlkShape* sh = reinterpret_cast<BlkShape*>(p);
+        p += blk_align((size_t)a.count * sizeof(BlkShape));
+        // pageable source: the call returns once the records are staged
+        if ((e = cudaMemcpyAsync(sh, var->shapes.data(), (size_t)a.count * sizeof(BlkShape),
+                                 cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return e;
+        a.shapes = sh;
+    }
     T* base = reinterpret_cast<T*>(p);
-    a.W = base;  base += (size_t)a.count * z.W;
-    a.Vw = base; base += (size_t)a.count * z.V;
-    a.G = base;  base += (size_t)a.count * z.G;
-    a.J = base;  base += (size_t)a.count * z.J;
+    a.W = base;  base += (size_t)nW;
+    a.Vw = base; base += (size_t)nV;
+    a.G = base;  base += (size_t)nG;
+    a.J = base;  base += (size_t)nJ;
     a.T = base;
 
-    cudaError_t e;
     const int heevj_smem = 2 * TWO * LDG * (int)sizeof(T) + InnerTables<T, NB>::bytes();
     const int fin_smem = (kBlkThreads / 32) * (int)sizeof(R) + 16 + 2 * (int)sizeof(T) +
                          a.N * ((int)sizeof(R) + 4) + 16;
@@ -50,11 +73,22 @@ cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stag
         return e;
 
     blk_load<T><<<a.count, kBlkThreads, 0, st>>>(a);
-    const dim3 gpair(a.count, z.L / 2);
-    const dim3 gupd(a.count, z.L / 2, (a.M + a.N + kUpdRows - 1) / kUpdRows);
+    const dim3 gpair(a.count, a.L / 2);
+    // row blocks of the update: all of them, unless the block pairs alone
+    // give more than about 16 CTAs per SM (then each CTA loops over several;
+    // the two-stage kernels take one row block per CTA)
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 152;
+    }
+    const long long pairs = (long long)a.count * (a.L / 2);
+    const int zrows = (a.M + a.N + kUpdRows - 1) / kUpdRows;
+    const int zcap = (int)std::max(1LL, (16LL * sms + pairs - 1) / pairs);
+    const dim3 gupd(a.count, a.L / 2, two_stage ? zrows : std::min(zrows, zcap));
     // one sweep: every round's stages, then the end-of-sweep bookkeeping
     auto sweep = [&](cudaStream_t s) -> cudaError_t {
-        for (int r = 0; r < z.L - 1; ++r) {
+        for (int r = 0; r < a.L - 1; ++r) {
             if constexpr (std::is_same<T, float>::value && NB >= 8)
                 blk_gram_f32<NB><<<gpair, kBlkThreads, 0, s>>>(a, r);
             else
@@ -126,12 +160,12 @@ cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stag
 
 template <class T>
 cudaError_t blk_run(int nb, const BlockedArgs& a, void* work, cudaStream_t st, bool two_stage, bool host_sync,
-                    cudaStream_t capture) {
+                    cudaStream_t capture, const BlkVarPlan* var = nullptr) {
     switch (nb) {
-        case 4: return blk_run_nb<T, 4>(a, work, st, two_stage, host_sync, capture);
-        case 8: return blk_run_nb<T, 8>(a, work, st, two_stage, host_sync, capture);
-        case 16: return blk_run_nb<T, 16>(a, work, st, two_stage, host_sync, capture);
-        case 32: return blk_run_nb<T, 32>(a, work, st, two_stage, host_sync, capture);
+        case 4: return blk_run_nb<T, 4>(a, work, st, two_stage, host_sync, capture, var);
+        case 8: return blk_run_nb<T, 8>(a, work, st, two_stage, host_sync, capture, var);
+        case 16: return blk_run_nb<T, 16>(a, work, st, two_stage, host_sync, capture, var);
+        case 32: return blk_run_nb<T, 32>(a, work, st, two_stage, host_sync, capture, var);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -142,4 +176,8 @@ cudaError_t blk_run(int nb, const BlockedArgs& a, void* work, cudaStream_t st, b
     cudaError_t bsvd::blocked_run_##TAG(int nb, const BlockedArgs& a, void* work, cudaStream_t st, \
                                         bool two_stage, bool host_sync, cudaStream_t capture) { \
         return blk_run<TYPE>(nb, a, work, st, two_stage, host_sync, capture);                   \
+    }                                                                                           \
+    cudaError_t bsvd::blocked_run_var_##TAG(int nb, const BlockedArgs& a, const BlkVarPlan& var, \
+                                            void* work, cudaStream_t st, cudaStream_t capture) {  \
+        return blk_run<TYPE>(nb, a, work, st, false, false, capture, &var);                     \
     }

@@ -5,8 +5,16 @@
 #include <stddef.h>
 
 #include <algorithm>
+#include <vector>
 
 namespace bsvd {
+
+// One matrix of a variable-shape batch: its working shape and where its
+// regions start in the workspace (elements from each region's base).
+struct BlkShape {
+    int M, N, trans, m, n, l, L, Np;
+    long long oW, oV, oG, oJ, oT;
+};
 
 // Arguments of the multi-kernel path (type-erased pointers).
 struct BlockedArgs {
@@ -33,6 +41,9 @@ struct BlockedArgs {
     int max_sweeps, inner_sweeps, flags;
     int masks;                 // Design-4
     int wantU, wantV;
+    // variable-shape batch: per-matrix shapes and offsets (device, count
+    // entries); the scalar shape fields above then hold the maxima
+    const BlkShape* shapes;
 };
 
 inline size_t blk_align(size_t x) { return (x + 255) & ~size_t(255); }
@@ -56,6 +67,34 @@ inline BlkSizes blk_sizes(int nb, int M, int N, bool two_stage) {
     const long long fin = (long long)M + (long long)N * N + N;       // finalisation: x, E, rank
     z.T = std::max(two_stage ? pairs * (M + N) * two : 0LL, fin);
     return z;
+}
+
+// A variable-shape batch (fused vector update, no two-stage temporary):
+// per-matrix shapes and offsets, the maxima, and the workspace bytes.
+struct BlkVarPlan {
+    std::vector<BlkShape> shapes;
+    int Mmax = 0, Nmax = 0, lmax = 2, Lmax = 2;
+    long long W = 0, V = 0, G = 0, J = 0, T = 0;   // region sizes (elements)
+    size_t bytes = 0;
+};
+
+inline void blk_var_plan(int nb, int count, const int* m, const int* n, size_t elt, BlkVarPlan& p) {
+    p = BlkVarPlan();
+    p.shapes.resize(count);
+    for (int b = 0; b < count; ++b) {
+        BlkShape& s = p.shapes[b];
+        s.m = m[b]; s.n = n[b]; s.trans = m[b] < n[b];
+        s.M = std::max(m[b], n[b]); s.N = std::min(m[b], n[b]);
+        const BlkSizes z = blk_sizes(nb, s.M, s.N, false);
+        s.l = z.l; s.L = z.L; s.Np = z.Np;
+        s.oW = p.W; s.oV = p.V; s.oG = p.G; s.oJ = p.J; s.oT = p.T;
+        p.W += z.W; p.V += z.V; p.G += z.G; p.J += z.J; p.T += z.T;
+        p.Mmax = std::max(p.Mmax, s.M); p.Nmax = std::max(p.Nmax, s.N);
+        p.lmax = std::max(p.lmax, s.l); p.Lmax = std::max(p.Lmax, s.L);
+    }
+    p.bytes = blk_align((size_t)count * 4 * sizeof(int)) + blk_align((size_t)count * (p.Lmax / 2) * sizeof(int)) +
+              blk_align(sizeof(int)) + blk_align((size_t)count * sizeof(BlkShape)) +
+              blk_align((size_t)(p.W + p.V + p.G + p.J + p.T) * elt);
 }
 
 inline size_t blk_bytes(int nb, int M, int N, int count, bool two_stage, size_t elt) {

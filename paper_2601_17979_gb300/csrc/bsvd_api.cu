@@ -39,6 +39,9 @@ struct bsvd_handle_s {
     int cap_device = -1;
     cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};   // host-buffer pipeline: H2D, D2H, 2nd compute
     int pipe_device = -1;
+    cudaStream_t split = nullptr;                          // split uneven batches: the multi-kernel part
+    cudaEvent_t split_ev[2] = {nullptr, nullptr};          // fork from, join to the caller's stream
+    int split_device = -1;
 };
 
 namespace {
@@ -102,7 +105,7 @@ bool resolve(const bsvd_opts* o, bool single, int N, Resolved& r) {
     std::memset(&z, 0, sizeof z);
     if (!o) o = &z;
     if (o->nb < 0 || o->max_sweeps < 0 || o->inner_sweeps < 0 || o->tol < 0 || o->path < 0 ||
-        o->path > BSVD_PATH_PERSISTENT || o->flags < 0 || o->flags > 63 || o->prec < 0 ||
+        o->path > BSVD_PATH_PERSISTENT || o->flags < 0 || o->flags > 127 || o->prec < 0 ||
         o->prec > BSVD_PREC_MIXED || (o->prec == BSVD_PREC_MIXED && single))
         return false;
     r.nb = o->nb ? o->nb : (N >= 48 ? 16 : (N >= 12 ? 8 : 4));
@@ -140,6 +143,8 @@ void apply_tuned(bsvd_handle h, char t, int m, int n, bool wantU, bool wantV, co
 typedef size_t (*plan_fn)(int, int, int, bool, FusedArgs&, int&);
 typedef cudaError_t (*launch_fn)(int, const FusedArgs&, int, size_t, cudaStream_t);
 typedef cudaError_t (*blocked_fn)(int, const BlockedArgs&, void*, cudaStream_t, bool, bool, cudaStream_t);
+typedef cudaError_t (*blocked_var_fn)(int, const BlockedArgs&, const bsvd::BlkVarPlan&, void*, cudaStream_t,
+                                      cudaStream_t);
 typedef cudaError_t (*persist_fn)(int, const bsvd::PersistArgs&, int, int, cudaStream_t);
 typedef long long (*slot_fn)(int, int, int);
 
@@ -151,18 +156,19 @@ struct TypeOps {
     blocked_fn blocked;
     persist_fn persist;
     slot_fn slot;
+    blocked_var_fn blocked_var;
 };
 
 TypeOps ops_for(char t) {
     switch (t) {
         case 's': return {true, 4, bsvd::fused_plan_s, bsvd::fused_launch_s, bsvd::blocked_run_s,
-                          bsvd::persist_launch_s, bsvd::persist_slot_s};
+                          bsvd::persist_launch_s, bsvd::persist_slot_s, bsvd::blocked_run_var_s};
         case 'd': return {false, 8, bsvd::fused_plan_d, bsvd::fused_launch_d, bsvd::blocked_run_d,
-                          bsvd::persist_launch_d, bsvd::persist_slot_d};
+                          bsvd::persist_launch_d, bsvd::persist_slot_d, bsvd::blocked_run_var_d};
         case 'c': return {true, 8, bsvd::fused_plan_c, bsvd::fused_launch_c, bsvd::blocked_run_c,
-                          bsvd::persist_launch_c, bsvd::persist_slot_c};
+                          bsvd::persist_launch_c, bsvd::persist_slot_c, bsvd::blocked_run_var_c};
         default:  return {false, 16, bsvd::fused_plan_z, bsvd::fused_launch_z, bsvd::blocked_run_z,
-                          bsvd::persist_launch_z, bsvd::persist_slot_z};
+                          bsvd::persist_launch_z, bsvd::persist_slot_z, bsvd::blocked_run_var_z};
     }
 }
 
@@ -567,10 +573,11 @@ int device_sms_or_default(bsvd_handle h) {
 }
 
 bsvd_status plan_persistent(int sms, const TypeOps& ops, int batch, const int* m, const int* n,
-                            const bsvd_opts* opts, PersistPlan& pp) {
+                            const bsvd_opts* opts, PersistPlan& pp, const std::vector<char>* excl = nullptr) {
     pp.maxN = 0;
     pp.order.clear();
     for (int i = 0; i < batch; ++i) {
+        if (excl && (*excl)[i]) continue;             // solved on the multi-kernel path
         const int k = std::min(m[i], n[i]);
         if (k > 0) pp.order.push_back(i);
         pp.maxN = std::max(pp.maxN, k);
@@ -600,9 +607,9 @@ bsvd_status persistent_impl(bsvd_handle h, const TypeOps& ops, bool wantU, bool 
                             void* const* dS, void* const* dU, const int* ldu, void* const* dV,
                             const int* ldv, int* d_info, int* d_sweeps, void* d_work,
                             size_t work_bytes, const bsvd_opts* opts, cudaStream_t s, int* d_done = nullptr,
-                            const int* d_abort = nullptr) {
+                            const int* d_abort = nullptr, const std::vector<char>* excl = nullptr) {
     PersistPlan pp;
-    bsvd_status st = plan_persistent(h->sm_count, ops, batch, m, n, opts, pp);
+    bsvd_status st = plan_persistent(h->sm_count, ops, batch, m, n, opts, pp, excl);
     if (st != BSVD_OK) return st;
     if (!d_work || work_bytes < pp.bytes) return BSVD_ERR_WORKSPACE;
     Resolved r;
@@ -650,6 +657,117 @@ bsvd_status persistent_impl(bsvd_handle h, const TypeOps& ops, bool wantU, bool 
     return e == cudaSuccess ? BSVD_OK : fail_cuda(h, e);
 }
 
+// ---- flags bit 6: split an uneven complex64 persistent batch ------------------
+// Matrices with min(m, n) >= kSplitK run on the multi-kernel path as one
+// variable-shape batch (per-matrix shapes, CUDA-graph sweeps) on a stream of
+// the handle, beside the persistent launch for the rest.  With W in global
+// memory the persistent kernel's inner solver runs four block pairs per SM;
+// the multi-kernel path runs every pair of every large matrix at once.
+// Measured on the uneven workload's 4,224 complex64 matrices with k >= 128:
+// 2.47 s against 3.11 s in the persistent launch (with flags bit 4; without
+// it the empty sweeps up to max_sweeps cost 0.3 s).  For FP32 the
+// variable-shape batch was slower (1.31 s against 1.20 s), so the flag
+// leaves other types in the persistent launch.
+constexpr int kFlagSplit = 64, kSplitK = 128;
+
+bool split_large(const TypeOps& ops, const bsvd_opts* opts) {
+    return ops.single && ops.elt == 8 && opts && opts->path == BSVD_PATH_PERSISTENT && (opts->flags & kFlagSplit);
+}
+
+struct SplitPlan {
+    std::vector<char> excl;        // by matrix id: on the multi-kernel path
+    std::vector<int> ids;          // those ids, in order
+    bsvd::BlkVarPlan var;
+    int nb = 16;
+    size_t ints = 0, bytes = 0;    // ids + lda, ldu, ldv (batch each); then the multi-kernel workspace
+};
+
+void plan_split(const TypeOps& ops, int batch, const int* m, const int* n, const bsvd_opts* opts, SplitPlan& sp) {
+    sp.excl.assign(batch, 0);
+    sp.ids.clear();
+    std::vector<int> mm, nn;
+    for (int i = 0; i < batch; ++i)
+        if (std::min(m[i], n[i]) >= kSplitK) {
+            sp.excl[i] = 1;
+            sp.ids.push_back(i);
+            mm.push_back(m[i]);
+            nn.push_back(n[i]);
+        }
+    sp.nb = (opts && opts->nb) ? opts->nb : 16;
+    const int count = (int)sp.ids.size();
+    bsvd::blk_var_plan(sp.nb, count, mm.data(), nn.data(), ops.elt, sp.var);
+    sp.ints = align256(((size_t)count + 3 * (size_t)batch) * sizeof(int));
+    sp.bytes = count ? sp.ints + align256(sp.var.bytes) : 0;
+}
+
+cudaError_t split_streams(bsvd_handle h) {
+    if (h->split && h->split_device == h->device) return cudaSuccess;
+    if (h->split) cudaStreamDestroy(h->split);
+    for (cudaEvent_t& ev : h->split_ev)
+        if (ev) cudaEventDestroy(ev);
+    h->split = nullptr;
+    h->split_ev[0] = h->split_ev[1] = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&h->split, cudaStreamNonBlocking);
+    for (cudaEvent_t& ev : h->split_ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) h->split_device = h->device;
+    return e;
+}
+
+bsvd_status split_impl(bsvd_handle h, const TypeOps& ops, bool wantU, bool wantV, int batch, const int* m,
+                       const int* n, const void* const* dA, const int* lda, void* const* dS, void* const* dU,
+                       const int* ldu, void* const* dV, const int* ldv, int* d_info, int* d_sweeps,
+                       void* d_work, size_t work_bytes, const bsvd_opts* opts, cudaStream_t s) {
+    SplitPlan sp;
+    plan_split(ops, batch, m, n, opts, sp);
+    PersistPlan pp;
+    bsvd_status st = plan_persistent(h->sm_count, ops, batch, m, n, opts, pp, &sp.excl);
+    if (st != BSVD_OK) return st;
+    if (!d_work || work_bytes < pp.bytes + sp.bytes) return BSVD_ERR_WORKSPACE;
+    const int count = (int)sp.ids.size();
+    Resolved r;
+    if (count > 0 && !resolve(opts, ops.single, sp.var.Nmax, r)) return fail_arg(h, 18);
+    cudaError_t e = cudaSuccess;
+    if (count > 0) {
+        if ((e = split_streams(h)) != cudaSuccess) return fail_cuda(h, e);
+        // fork: the side stream starts after the work already queued on the caller's
+        if ((e = cudaEventRecord(h->split_ev[0], s)) != cudaSuccess) return fail_cuda(h, e);
+    }
+    // the persistent launch first: with flags bit 4 the multi-kernel part
+    // below returns only once its matrices have converged
+    st = persistent_impl(h, ops, wantU, wantV, batch, m, n, dA, lda, dS, dU, ldu, dV, ldv, d_info, d_sweeps,
+                         d_work, pp.bytes, opts, s, nullptr, nullptr, &sp.excl);
+    if (st != BSVD_OK || count == 0) return st;
+    cudaStream_t side = h->split;
+    if ((e = cudaStreamWaitEvent(side, h->split_ev[0], 0)) != cudaSuccess) return fail_cuda(h, e);
+    char* reg = static_cast<char*>(d_work) + pp.bytes;
+    std::vector<int> host(sp.ids);
+    host.resize((size_t)count + 3 * (size_t)batch);
+    for (int i = 0; i < batch; ++i) {
+        host[count + i] = lda[i];
+        host[count + batch + i] = wantU ? ldu[i] : 1;
+        host[count + 2 * (size_t)batch + i] = wantV ? ldv[i] : 1;
+    }
+    int* dints = reinterpret_cast<int*>(reg);
+    e = cudaMemcpyAsync(dints, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice, side);
+    if (e == cudaSuccess) {
+        BlockedArgs a = blocked_args(1, 1, count, wantU, wantV, r, true);
+        a.Ap = dA; a.ldap = dints + count;
+        a.Sp = dS;
+        a.Up = dU; a.ldup = dints + count + batch;
+        a.Vp = dV; a.ldvp = dints + count + 2 * batch;
+        a.index = dints;
+        a.info = d_info;
+        a.sweeps = d_sweeps;
+        e = ops.blocked_var(sp.nb, a, sp.var, reg + sp.ints, side, capture_stream(h, r.flags));
+    }
+    // join, also after a failure: the caller's stream owns the results
+    cudaError_t ej = cudaEventRecord(h->split_ev[1], side);
+    if (ej == cudaSuccess) ej = cudaStreamWaitEvent(s, h->split_ev[1], 0);
+    if (e == cudaSuccess) e = ej;
+    return e == cudaSuccess ? BSVD_OK : fail_cuda(h, e);
+}
+
 bsvd_status batched_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, int batch,
                          const int* m, const int* n, const void* const* dA, const int* lda,
                          void* const* dS, void* const* dU, const int* ldu, void* const* dV,
@@ -684,6 +802,9 @@ bsvd_status batched_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
     if (opts && opts->path == BSVD_PATH_PERSISTENT) {
         bsvd_status st = refresh_device(h);
         if (st != BSVD_OK) return st;
+        if (split_large(ops, opts))
+            return split_impl(h, ops, wantU, wantV, batch, m, n, dA, lda, dS, dU, ldu, dV, ldv, d_info,
+                              d_sweeps, d_work, work_bytes, opts, static_cast<cudaStream_t>(stream));
         return persistent_impl(h, ops, wantU, wantV, batch, m, n, dA, lda, dS, dU, ldu, dV, ldv, d_info,
                                d_sweeps, d_work, work_bytes, opts, static_cast<cudaStream_t>(stream));
     }
@@ -845,9 +966,13 @@ bsvd_status bsvd_create(bsvd_handle* handle) {
 
 bsvd_status bsvd_destroy(bsvd_handle handle) {
     if (handle && handle->cap) cudaStreamDestroy(handle->cap);
-    if (handle)
+    if (handle) {
         for (cudaStream_t s : handle->pipe)
             if (s) cudaStreamDestroy(s);
+        if (handle->split) cudaStreamDestroy(handle->split);
+        for (cudaEvent_t ev : handle->split_ev)
+            if (ev) cudaEventDestroy(ev);
+    }
     delete handle;
     return BSVD_OK;
 }
@@ -921,9 +1046,13 @@ bsvd_status bsvd_gesvj_workspace(bsvd_handle handle, char dtype, int batch, cons
     if (opts && opts->prec == BSVD_PREC_MIXED) return BSVD_ERR_NOT_IMPLEMENTED;   // strided form only
     if (opts && (opts->flags & kFlagQR)) return BSVD_ERR_NOT_IMPLEMENTED;      // strided form only
     if (opts && opts->path == BSVD_PATH_PERSISTENT) {
+        SplitPlan sp;
+        const bool split = split_large(ops, opts);
+        if (split) plan_split(ops, batch, m_arr, n_arr, opts, sp);
         PersistPlan pp;
-        bsvd_status st = plan_persistent(device_sms_or_default(handle), ops, batch, m_arr, n_arr, opts, pp);
-        if (st == BSVD_OK) *bytes = pp.bytes;
+        bsvd_status st = plan_persistent(device_sms_or_default(handle), ops, batch, m_arr, n_arr, opts, pp,
+                                         split ? &sp.excl : nullptr);
+        if (st == BSVD_OK) *bytes = pp.bytes + (split ? sp.bytes : 0);
         return st;
     }
     std::vector<Plan> plans;

@@ -24,6 +24,24 @@ enum : int { kBlkThreads = 256, kUpdRows = 128, kGramChunk = 64 };
 
 __device__ __forceinline__ int blk_mid(const BlockedArgs& a, int b) { return a.index ? a.index[b] : b; }
 
+// working shape of matrix b and its offsets in the workspace regions: the
+// per-matrix record of a variable-shape batch, else the batch's one shape
+__device__ __forceinline__ BlkShape blk_shape(const BlockedArgs& a, int b) {
+    if (a.shapes) return a.shapes[b];
+    BlkShape s;
+    s.M = a.M; s.N = a.N; s.trans = a.trans; s.m = a.m; s.n = a.n; s.l = a.l; s.L = a.L; s.Np = a.Np;
+    s.oW = b * a.sW; s.oV = b * a.sVw; s.oG = b * a.sG; s.oJ = b * a.sJ; s.oT = b * a.sT;
+    return s;
+}
+
+// block pair q of round r of matrix b, or false when the matrix has no such
+// pair (a phantom block, or a round or pair beyond a smaller matrix's count)
+__device__ __forceinline__ bool blk_pair(const BlkShape& s, int r, int q, int& bi, int& bj) {
+    if (r >= s.L - 1 || q >= s.L / 2) return false;
+    rr_pair(s.L, r, q, bi, bj);
+    return bj < s.l;
+}
+
 // skip this matrix? (bad input always; converged ones only with masks)
 __device__ __forceinline__ bool blk_skip(const BlockedArgs& a, int b) {
     const int st = a.state[4 * b];
@@ -46,11 +64,11 @@ __global__ void __launch_bounds__(kBlkThreads) blk_gram_f32(const BlockedArgs a,
     __shared__ __align__(16) float P[KP * TWO];
     const int b = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
     if (blk_skip(a, b)) return;
+    const BlkShape sh = blk_shape(a, b);
     int bi, bj;
-    rr_pair(a.L, r, q, bi, bj);
-    if (bj >= a.l) return;
-    const float* W = static_cast<const float*>(a.W) + b * a.sW;
-    const int M = a.M;
+    if (!blk_pair(sh, r, q, bi, bj)) return;
+    const float* W = static_cast<const float*>(a.W) + sh.oW;
+    const int M = sh.M;
     const int tile = tid / KS, ks = tid % KS, ti = tile / TT, tj = tile % TT;
     float acc[4][4];
 #pragma unroll
@@ -93,7 +111,7 @@ __global__ void __launch_bounds__(kBlkThreads) blk_gram_f32(const BlockedArgs a,
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] += __shfl_xor_sync(0xffffffffu, acc[i][j], o);
-    float* G = static_cast<float*>(a.G) + b * a.sG + (long long)q * TWO * TWO;
+    float* G = static_cast<float*>(a.G) + sh.oG + (long long)q * TWO * TWO;
     if (ks == 0 && ti <= tj) {
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -115,12 +133,13 @@ __global__ void __launch_bounds__(kBlkThreads) blk_load(const BlockedArgs a) {
     __shared__ int bad_s, ex_s;
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int mid = blk_mid(a, b);
+    const BlkShape sh = blk_shape(a, b);
     const T* A = a.Ap ? static_cast<const T*>(a.Ap[mid]) : static_cast<const T*>(a.A) + (long long)mid * a.sA;
     const int lda = a.ldap ? a.ldap[mid] : a.lda;
     R mx = 0;
     int nonfin = 0;
-    for (int e = tid; e < a.m * a.n; e += NT) {
-        const T x = A[(e % a.m) + (long long)(e / a.m) * lda];
+    for (int e = tid; e < sh.m * sh.n; e += NT) {
+        const T x = A[(e % sh.m) + (long long)(e / sh.m) * lda];
         if (!finite_s(x)) nonfin = 1; else mx = fmax(mx, maxabs(x));
     }
     mx = warp_max(mx);
@@ -141,18 +160,18 @@ __global__ void __launch_bounds__(kBlkThreads) blk_load(const BlockedArgs a) {
     __syncthreads();
     if (bad_s) return;
     const int ex = ex_s;
-    T* W = static_cast<T*>(a.W) + b * a.sW;
-    T* V = static_cast<T*>(a.Vw) + b * a.sVw;
-    const int M = a.M, N = a.N;
-    for (int e = tid; e < a.m * a.n; e += NT) {
-        const int i = e % a.m, j = e / a.m;
+    T* W = static_cast<T*>(a.W) + sh.oW;
+    T* V = static_cast<T*>(a.Vw) + sh.oV;
+    const int M = sh.M, N = sh.N;
+    for (int e = tid; e < sh.m * sh.n; e += NT) {
+        const int i = e % sh.m, j = e / sh.m;
         const T x = scalb_s(A[i + (long long)j * lda], -ex);
-        if (a.trans) W[j + (long long)i * M] = conj_s(x);
-        else         W[i + (long long)j * M] = x;
+        if (sh.trans) W[j + (long long)i * M] = conj_s(x);
+        else          W[i + (long long)j * M] = x;
     }
-    for (int e = tid; e < M * (a.Np - N); e += NT) W[(e % M) + (long long)(N + e / M) * M] = make_s<T>(0);
+    for (int e = tid; e < M * (sh.Np - N); e += NT) W[(e % M) + (long long)(N + e / M) * M] = make_s<T>(0);
     const T* V0 = a.V0 ? static_cast<const T*>(a.V0) + (long long)mid * a.sV0 : nullptr;
-    for (int e = tid; e < N * a.Np; e += NT) {
+    for (int e = tid; e < N * sh.Np; e += NT) {
         const int i = e % N, j = e / N;
         V[i + (long long)j * N] = (V0 && j < N) ? V0[i + (long long)j * a.ldv0] : make_s<T>(i == j && !V0 ? 1 : 0);
     }
@@ -174,11 +193,11 @@ __global__ void __launch_bounds__(kBlkThreads) blk_gram(const BlockedArgs a, int
     __shared__ T P[KP * TWO];
     const int b = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
     if (blk_skip(a, b)) return;
+    const BlkShape sh = blk_shape(a, b);
     int bi, bj;
-    rr_pair(a.L, r, q, bi, bj);
-    if (bj >= a.l) return;
-    const T* W = static_cast<const T*>(a.W) + b * a.sW;
-    const int M = a.M;
+    if (!blk_pair(sh, r, q, bi, bj)) return;
+    const T* W = static_cast<const T*>(a.W) + sh.oW;
+    const int M = sh.M;
     // two partial sums per entry, rows [0, M/2) and [M/2, M), added at the end
     // (the same summation as the on-chip kernel)
     T lo[PER], hi[PER];
@@ -213,7 +232,7 @@ __global__ void __launch_bounds__(kBlkThreads) blk_gram(const BlockedArgs a, int
     T acc[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u) acc[u] = add(lo[u], hi[u]);
-    T* G = static_cast<T*>(a.G) + b * a.sG + (long long)q * TWO * TWO;
+    T* G = static_cast<T*>(a.G) + sh.oG + (long long)q * TWO * TWO;
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
         const int e = tid + u * NT;
@@ -236,13 +255,13 @@ __global__ void __launch_bounds__(GT) blk_heevj(const BlockedArgs a, int r) {
     const int b = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
     int* pf = a.pairflag + (long long)b * (a.L / 2) + q;
     if (blk_skip(a, b)) { if (tid == 0) *pf = 0; return; }
+    const BlkShape sh = blk_shape(a, b);
     int bi, bj;
-    rr_pair(a.L, r, q, bi, bj);
-    if (bj >= a.l) { if (tid == 0) *pf = 0; return; }
+    if (!blk_pair(sh, r, q, bi, bj)) { if (tid == 0) *pf = 0; return; }
     T* G = reinterpret_cast<T*>(smem);
     T* J = G + TWO * LDG;
     const InnerTables<T, NB> tb(J + TWO * LDG);
-    const T* Gg = static_cast<const T*>(a.G) + b * a.sG + (long long)q * TWO * TWO;
+    const T* Gg = static_cast<const T*>(a.G) + sh.oG + (long long)q * TWO * TWO;
     for (int e = tid; e < TWO * TWO; e += GT) {       // upper triangle, mirrored
         const int i = e % TWO, j = e / TWO;
         if (i > j) continue;
@@ -253,7 +272,7 @@ __global__ void __launch_bounds__(GT) blk_heevj(const BlockedArgs a, int r) {
     }
     __syncthreads();
     const int seen = inner_jacobi<T, NB, GT>(G, J, tb, (Real<T>)a.tol, a.inner_sweeps, tid, 1);
-    T* Jg = static_cast<T*>(a.J) + b * a.sJ + (long long)q * TWO * TWO;
+    T* Jg = static_cast<T*>(a.J) + sh.oJ + (long long)q * TWO * TWO;
     for (int e = tid; e < TWO * TWO; e += GT) Jg[(e % TWO) + (e / TWO) * TWO] = J[(e % TWO) + (e / TWO) * LDG];
     if (tid == 0) {
         *pf = seen > 0;
@@ -263,14 +282,17 @@ __global__ void __launch_bounds__(GT) blk_heevj(const BlockedArgs a, int r) {
 
 // panel row helpers: row `row` of [W; V] (rows 0..M-1 of W, then N of V)
 template <class T>
-__device__ __forceinline__ T* blk_row(const BlockedArgs& a, int b, int row, long long& ld) {
-    if (row < a.M) { ld = a.M; return static_cast<T*>(a.W) + b * a.sW + row; }
-    ld = a.N;
-    return static_cast<T*>(a.Vw) + b * a.sVw + (row - a.M);
+__device__ __forceinline__ T* blk_row(const BlockedArgs& a, const BlkShape& sh, int row, long long& ld) {
+    if (row < sh.M) { ld = sh.M; return static_cast<T*>(a.W) + sh.oW + row; }
+    ld = sh.N;
+    return static_cast<T*>(a.Vw) + sh.oV + (row - sh.M);
 }
 
 // ---- S4/S5 fused (Design-3, Alg. 4): [P_i P_j] <- [P_i P_j] J, one read and one
 // write per element.  grid (count, L/2, row blocks), kUpdRows threads.
+// Row blocks z, z + gridDim.z, ...: the launcher caps gridDim.z once the
+// batch has enough block pairs to fill the GPU, so that masked (converged)
+// matrices and pairs cost fewer empty CTAs per launch.
 template <class T, int NB>
 __global__ void __launch_bounds__(kUpdRows) blk_update_fused(const BlockedArgs a, int r) {
     constexpr int TWO = 2 * NB;
@@ -279,25 +301,27 @@ __global__ void __launch_bounds__(kUpdRows) blk_update_fused(const BlockedArgs a
     const int b = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
     if (blk_skip(a, b)) return;
     if (a.masks && !a.pairflag[(long long)b * (a.L / 2) + q]) return;
+    const BlkShape sh = blk_shape(a, b);
     int bi, bj;
-    rr_pair(a.L, r, q, bi, bj);
-    if (bj >= a.l) return;
-    const T* Jg = static_cast<const T*>(a.J) + b * a.sJ + (long long)q * TWO * TWO;
+    if (!blk_pair(sh, r, q, bi, bj)) return;
+    const int rows = sh.M + sh.N;
+    if (blockIdx.z * kUpdRows >= rows) return;
+    const T* Jg = static_cast<const T*>(a.J) + sh.oJ + (long long)q * TWO * TWO;
     for (int e = tid; e < TWO * TWO; e += kUpdRows) Js[e] = Jg[e];
     __syncthreads();
-    const int row = blockIdx.z * kUpdRows + tid;
-    if (row >= a.M + a.N) return;
-    long long ld;
-    T* X = blk_row<T>(a, b, row, ld);
-    T x[TWO];
+    for (int row = blockIdx.z * kUpdRows + tid; row < rows; row += gridDim.z * kUpdRows) {
+        long long ld;
+        T* X = blk_row<T>(a, sh, row, ld);
+        T x[TWO];
 #pragma unroll
-    for (int k = 0; k < TWO; ++k) x[k] = X[(long long)(k < NB ? bi * NB + k : bj * NB + k - NB) * ld];
+        for (int k = 0; k < TWO; ++k) x[k] = X[(long long)(k < NB ? bi * NB + k : bj * NB + k - NB) * ld];
 #pragma unroll
-    for (int c = 0; c < TWO; ++c) {
-        T acc = make_s<T>(0);
+        for (int c = 0; c < TWO; ++c) {
+            T acc = make_s<T>(0);
 #pragma unroll
-        for (int k = 0; k < TWO; ++k) acc = fma_s(x[k], Js[k + c * TWO], acc);
-        X[(long long)(c < NB ? bi * NB + c : bj * NB + c - NB) * ld] = acc;
+            for (int k = 0; k < TWO; ++k) acc = fma_s(x[k], Js[k + c * TWO], acc);
+            X[(long long)(c < NB ? bi * NB + c : bj * NB + c - NB) * ld] = acc;
+        }
     }
 }
 
@@ -310,17 +334,18 @@ __global__ void __launch_bounds__(kUpdRows) blk_update_stage1(const BlockedArgs 
     const int b = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
     if (blk_skip(a, b)) return;
     if (a.masks && !a.pairflag[(long long)b * (a.L / 2) + q]) return;
+    const BlkShape sh = blk_shape(a, b);
     int bi, bj;
-    rr_pair(a.L, r, q, bi, bj);
-    if (bj >= a.l) return;
-    const T* Jg = static_cast<const T*>(a.J) + b * a.sJ + (long long)q * TWO * TWO;
+    if (!blk_pair(sh, r, q, bi, bj)) return;
+    if (blockIdx.z * kUpdRows >= sh.M + sh.N) return;
+    const T* Jg = static_cast<const T*>(a.J) + sh.oJ + (long long)q * TWO * TWO;
     for (int e = tid; e < TWO * TWO; e += kUpdRows) Js[e] = Jg[e];
     __syncthreads();
-    const int row = blockIdx.z * kUpdRows + tid, rows = a.M + a.N;
+    const int row = blockIdx.z * kUpdRows + tid, rows = sh.M + sh.N;
     if (row >= rows) return;
     long long ld;
-    const T* X = blk_row<T>(a, b, row, ld);
-    T* Tt = static_cast<T*>(a.T) + b * a.sT + (long long)q * rows * TWO + row;
+    const T* X = blk_row<T>(a, sh, row, ld);
+    T* Tt = static_cast<T*>(a.T) + sh.oT + (long long)q * rows * TWO + row;
     T x[NB];
 #pragma unroll
     for (int k = 0; k < NB; ++k) x[k] = X[(long long)(bi * NB + k) * ld];
@@ -342,17 +367,18 @@ __global__ void __launch_bounds__(kUpdRows) blk_update_stage2(const BlockedArgs 
     const int b = blockIdx.x, q = blockIdx.y, tid = threadIdx.x;
     if (blk_skip(a, b)) return;
     if (a.masks && !a.pairflag[(long long)b * (a.L / 2) + q]) return;
+    const BlkShape sh = blk_shape(a, b);
     int bi, bj;
-    rr_pair(a.L, r, q, bi, bj);
-    if (bj >= a.l) return;
-    const T* Jg = static_cast<const T*>(a.J) + b * a.sJ + (long long)q * TWO * TWO;
+    if (!blk_pair(sh, r, q, bi, bj)) return;
+    if (blockIdx.z * kUpdRows >= sh.M + sh.N) return;
+    const T* Jg = static_cast<const T*>(a.J) + sh.oJ + (long long)q * TWO * TWO;
     for (int e = tid; e < TWO * TWO; e += kUpdRows) Js[e] = Jg[e];
     __syncthreads();
-    const int row = blockIdx.z * kUpdRows + tid, rows = a.M + a.N;
+    const int row = blockIdx.z * kUpdRows + tid, rows = sh.M + sh.N;
     if (row >= rows) return;
     long long ld;
-    T* X = blk_row<T>(a, b, row, ld);
-    const T* Tt = static_cast<const T*>(a.T) + b * a.sT + (long long)q * rows * TWO + row;
+    T* X = blk_row<T>(a, sh, row, ld);
+    const T* Tt = static_cast<const T*>(a.T) + sh.oT + (long long)q * rows * TWO + row;
     T x[NB];
 #pragma unroll
     for (int k = 0; k < NB; ++k) x[k] = X[(long long)(bj * NB + k) * ld];
@@ -382,8 +408,8 @@ static __global__ void blk_converge(const BlockedArgs a) {
 // rank of each column of a finished matrix, kept in the finalisation scratch
 // after x (M) and E (N x N)
 template <class T>
-__device__ __forceinline__ int* fin_rank(const BlockedArgs& a, int b) {
-    return reinterpret_cast<int*>(static_cast<T*>(a.T) + b * a.sT + a.M + (long long)a.N * a.N);
+__device__ __forceinline__ int* fin_rank(const BlockedArgs& a, const BlkShape& sh) {
+    return reinterpret_cast<int*>(static_cast<T*>(a.T) + sh.oT + sh.M + (long long)sh.N * sh.N);
 }
 
 template <class T>
@@ -393,7 +419,8 @@ __global__ void __launch_bounds__(kBlkThreads) blk_finalize(const BlockedArgs a)
     extern __shared__ __align__(16) unsigned char smem[];
     const int b = blockIdx.x, tid = threadIdx.x;
     const int mid = blk_mid(a, b);
-    const int N = a.N, M = a.M;
+    const BlkShape sh = blk_shape(a, b);
+    const int N = sh.N, M = sh.M;
     R* red = reinterpret_cast<R*>(smem);                 // [NT/32]
     int* iscr = reinterpret_cast<int*>(red + NT / 32);   // [4]
     T* bcast = reinterpret_cast<T*>(iscr + 4);           // [2]
@@ -414,25 +441,25 @@ __global__ void __launch_bounds__(kBlkThreads) blk_finalize(const BlockedArgs a)
     const int status = a.state[4 * b], sw = a.state[4 * b + 2], ex = a.state[4 * b + 3];
     if (status < 0) {
         for (int e = tid; e < N; e += NT) Sout[e] = nan_s<R>();
-        if (Uout) for (int e = tid; e < a.m * N; e += NT) Uout[(e % a.m) + (long long)(e / a.m) * ldu] = nan_s<T>();
-        if (Vout) for (int e = tid; e < a.n * N; e += NT) Vout[(e % a.n) + (long long)(e / a.n) * ldv] = nan_s<T>();
+        if (Uout) for (int e = tid; e < sh.m * N; e += NT) Uout[(e % sh.m) + (long long)(e / sh.m) * ldu] = nan_s<T>();
+        if (Vout) for (int e = tid; e < sh.n * N; e += NT) Vout[(e % sh.n) + (long long)(e / sh.n) * ldv] = nan_s<T>();
         if (tid == 0) {
             a.info[mid] = -1;
             if (a.sweeps) a.sweeps[mid] = 0;
         }
         return;
     }
-    const T* W = static_cast<const T*>(a.W) + b * a.sW;
-    const T* V = static_cast<const T*>(a.Vw) + b * a.sVw;
-    T* scratch = static_cast<T*>(a.T) + b * a.sT;        // x (M), E (N x N), rank (N)
-    const bool wantWout = a.trans ? a.wantV : a.wantU;
-    T* Y = a.trans ? Vout : Uout;
+    const T* W = static_cast<const T*>(a.W) + sh.oW;
+    const T* V = static_cast<const T*>(a.Vw) + sh.oV;
+    T* scratch = static_cast<T*>(a.T) + sh.oT;           // x (M), E (N x N), rank (N)
+    const bool wantWout = sh.trans ? a.wantV : a.wantU;
+    T* Y = sh.trans ? Vout : Uout;
     const FinalScratch<T> fs{sig, rank, red, iscr, bcast};
     // Sigma and U here; V (and its Newton-Schulz step) in the tiled kernels
     // below, which read the columns' ranks from the workspace
     finalize_outputs<T, NT>(W, M, V, N, M, N, ex, scratch, scratch + M, N,
-                            false, Sout, Y, a.trans ? ldv : ldu, wantWout, nullptr, 1, false, fs);
-    int* grank = fin_rank<T>(a, b);
+                            false, Sout, Y, sh.trans ? ldv : ldu, wantWout, nullptr, 1, false, fs);
+    int* grank = fin_rank<T>(a, sh);
     for (int k = tid; k < N; k += NT) grank[k] = rank[k];
     if (tid == 0) {
         a.info[mid] = status == 0 ? 0 : sw;
@@ -470,20 +497,21 @@ __device__ __forceinline__ void fin_mac(T (&acc)[4][4], const T (*As)[kFinBT + 1
     }
 }
 
-template <class T>
-__device__ __forceinline__ bool fin_skip(const BlockedArgs& a, int b) {
-    return a.state[4 * b] < 0 || !(a.trans ? a.wantU : a.wantV);
+__device__ __forceinline__ bool fin_skip(const BlockedArgs& a, const BlkShape& sh, int b) {
+    return a.state[4 * b] < 0 || !(sh.trans ? a.wantU : a.wantV);
 }
 
 template <class T>
 __global__ void __launch_bounds__(kFinThreads) blk_fin_gram(const BlockedArgs a) {
     using R = Real<T>;
     const int b = blockIdx.x, ta = blockIdx.y, tb = blockIdx.z, tid = threadIdx.x;
-    if (ta > tb || fin_skip<T>(a, b)) return;
+    if (ta > tb) return;
+    const BlkShape sh = blk_shape(a, b);
+    const int N = sh.N, r0 = ta * kFinBT, c0 = tb * kFinBT, tr = tid & 15, tc = tid >> 4;
+    if (c0 >= N || fin_skip(a, sh, b)) return;
     __shared__ T As[kFinKC][kFinBT + 1], Bs[kFinKC][kFinBT + 1];
-    const int N = a.N, r0 = ta * kFinBT, c0 = tb * kFinBT, tr = tid & 15, tc = tid >> 4;
-    const T* V = static_cast<const T*>(a.Vw) + b * a.sVw;                // N x N, ld N
-    T* E = static_cast<T*>(a.T) + b * a.sT + a.M;                         // N x N, ld N
+    const T* V = static_cast<const T*>(a.Vw) + sh.oV;                    // N x N, ld N
+    T* E = static_cast<T*>(a.T) + sh.oT + sh.M;                           // N x N, ld N
     const T zero = make_s<T>(0);
     T acc[4][4];
 #pragma unroll
@@ -517,17 +545,18 @@ template <class T>
 __global__ void __launch_bounds__(kFinThreads) blk_fin_z(const BlockedArgs a) {
     using R = Real<T>;
     const int b = blockIdx.x, ti = blockIdx.y, tk = blockIdx.z, tid = threadIdx.x;
-    if (fin_skip<T>(a, b)) return;
+    const BlkShape sh = blk_shape(a, b);
+    const int N = sh.N, r0 = ti * kFinBT, c0 = tk * kFinBT, tr = tid & 15, tc = tid >> 4;
+    if (r0 >= N || c0 >= N || fin_skip(a, sh, b)) return;
     __shared__ T As[kFinKC][kFinBT + 1], Bs[kFinKC][kFinBT + 1];
-    const int N = a.N, r0 = ti * kFinBT, c0 = tk * kFinBT, tr = tid & 15, tc = tid >> 4;
     const bool correct = !(a.flags & 1);
-    const T* V = static_cast<const T*>(a.Vw) + b * a.sVw;
-    const T* E = static_cast<const T*>(a.T) + b * a.sT + a.M;
-    const int* rank = fin_rank<T>(a, b);
+    const T* V = static_cast<const T*>(a.Vw) + sh.oV;
+    const T* E = static_cast<const T*>(a.T) + sh.oT + sh.M;
+    const int* rank = fin_rank<T>(a, sh);
     const int mid = blk_mid(a, b);
     T* Z;
     long long ldz;
-    if (a.trans) {
+    if (sh.trans) {
         Z = a.Up ? static_cast<T*>(a.Up[mid]) : static_cast<T*>(a.U) + (long long)mid * a.sU;
         ldz = a.ldup ? a.ldup[mid] : a.ldu;
     } else {

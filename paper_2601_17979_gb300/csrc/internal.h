@@ -11,6 +11,7 @@ namespace bsvd {
 
 struct FusedArgs;
 struct BlockedArgs;
+struct BlkVarPlan;
 struct PersistArgs;
 
 // Buffers of the mixed-precision path (strided batches; per matrix, in the
@@ -76,7 +77,9 @@ bsvd_status persistent_with_flags(bsvd_handle h, char t, bool wantU, bool wantV,
 
 #define BSVD_DECLARE_BLOCKED(TAG)                                                               \
     cudaError_t blocked_run_##TAG(int nb, const BlockedArgs& a, void* work, cudaStream_t st,   \
-                                  bool two_stage, bool host_sync, cudaStream_t capture);
+                                  bool two_stage, bool host_sync, cudaStream_t capture);       \
+    cudaError_t blocked_run_var_##TAG(int nb, const BlockedArgs& a, const BlkVarPlan& var,      \
+                                      void* work, cudaStream_t st, cudaStream_t capture);
 
 BSVD_DECLARE_BLOCKED(s)
 BSVD_DECLARE_BLOCKED(d)

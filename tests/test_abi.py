@@ -182,3 +182,30 @@ def test_flat_outputs_layout():
         ends = off + m * k
         assert (ends[:-1] <= off[1:]).all() and ends[-1] <= flat.numel()
         assert (ptr.numpy() - flat.data_ptr() == off * elt).all()
+
+
+def test_split_workspace_query(L):
+    """Flags bit 6 on a persistent complex64 batch adds the variable-shape
+    multi-kernel workspace for the matrices with min(m, n) >= 128 only;
+    batches of the other types ignore the flag."""
+    h = bsvd.handle()
+    n = ctypes.c_size_t()
+    ms = (ctypes.c_int * 4)(300, 40, 200, 512)
+    ns = (ctypes.c_int * 4)(150, 30, 90, 256)
+    pers = binding.make_opts(path="persistent")
+    split = binding.make_opts(path="persistent", flags=binding.FLAG_SPLIT_LARGE)
+    sizes = {}
+    for t in (b"s", b"c", b"d", b"z"):
+        for name, o in (("pers", pers), ("split", split)):
+            assert L.bsvd_gesvj_workspace(h, t, 4, ms, ns, 0, 1, 1, ctypes.byref(o), ctypes.byref(n)) == 0
+            sizes[t, name] = n.value
+    # the two large matrices' W, V and finalisation scratch at least
+    big = sum(M * N + N * N * 2 + M for M, N in ((300, 150), (512, 256)))
+    assert sizes[b"c", "split"] > big * 8
+    for t in (b"s", b"d", b"z"):
+        assert sizes[t, "split"] == sizes[t, "pers"]
+    small = (ctypes.c_int * 2)(100, 60)
+    assert L.bsvd_gesvj_workspace(h, b"c", 2, small, small, 0, 1, 1, ctypes.byref(pers), ctypes.byref(n)) == 0
+    a = n.value
+    assert L.bsvd_gesvj_workspace(h, b"c", 2, small, small, 0, 1, 1, ctypes.byref(split), ctypes.byref(n)) == 0
+    assert n.value == a                          # nothing reaches the multi-kernel path

@@ -93,3 +93,53 @@ def test_persistent_jobs_none():
     ref = oracle.gesvj(mats, want_u=False, want_v=False)
     for i in range(len(mats)):
         assert np.abs(S[i] - ref["S"][i]).max() <= 50 * min(mats[i].shape) * checks.U32 * ref["S"][i][0]
+
+
+@pytest.mark.parametrize("dtype", [np.complex64, np.float32])
+def test_split_large_bitwise(dtype):
+    """Flags bit 6: complex64 matrices with min(m, n) >= 128 run as one
+    variable-shape multi-kernel batch beside the persistent launch.  Each of
+    them gets the bits of the multi-kernel path run on its shape alone (the
+    kernels do the same per-matrix arithmetic; rounds and pairs a smaller
+    matrix lacks are skipped), each of the rest the bits of the plain
+    persistent launch.  FP32 batches ignore the flag."""
+    rng = np.random.default_rng(31)
+    shapes = [(300, 150), (40, 30), (128, 128), (140, 260), (64, 20), (513, 129), (90, 90), (0, 4), (200, 131)]
+    cplx = np.issubdtype(dtype, np.complexfloating)
+    mats = [(rng.uniform(-1, 1, s) + (1j * rng.uniform(-1, 1, s) if cplx else 0)).astype(dtype) for s in shapes]
+    S, U, V, info, sw = run_batched(mats, path="persistent", flags=bsvd.FLAG_SPLIT_LARGE)
+    Sp, Up, Vp, ip, wp = run_batched(mats, path="persistent")
+    assert (info == 0).all() and (ip == 0).all()
+    u = checks.unit_roundoff(dtype)
+    for k, (A, (m, n)) in enumerate(zip(mats, shapes)):
+        if min(m, n) == 0:
+            continue
+        if min(m, n) >= 128 and cplx:
+            S1, U1, V1, i1, w1 = run_batched([A], path="blocked", nb=16)
+        else:
+            S1, U1, V1, i1, w1 = [Sp[k]], [Up[k]], [Vp[k]], [ip[k]], [wp[k]]
+        assert sw[k] == w1[0], (k, sw[k], w1[0])
+        assert np.array_equal(S[k], S1[0]) and np.array_equal(U[k], U1[0]) and np.array_equal(V[k], V1[0]), k
+        meas = checks.measures(A, S[k], U[k], V[k], oracle.gesvj(A)["S"])
+        assert checks.violations(meas, u) == [], (k, A.shape, meas)
+
+
+@pytest.mark.parametrize("cplx", [True])
+def test_split_large_uneven_sample_and_jobs(cplx):
+    """The uneven workload's recipe with the split, parity with the oracle;
+    then without U and V."""
+    pool = [(i, synth.matrix("uneven", i)) for i in range(1 if cplx else 0, 160, 2)]
+    big = [x for _, x in pool if min(x.shape) >= 128][:4]
+    small = [x for _, x in pool if min(x.shape) < 128][:6]
+    mats = big + small
+    S, U, V, info, sw = run_batched(mats, path="persistent", flags=bsvd.FLAG_SPLIT_LARGE | bsvd.FLAG_SYNC_CHECK)
+    ref = oracle.gesvj(mats)
+    assert (info == 0).all(), info
+    for i, A in enumerate(mats):
+        meas = checks.measures(A, S[i], U[i], V[i], ref["S"][i])
+        assert checks.violations(meas, checks.U32) == [], (i, A.shape, meas)
+    S2, U2, V2, i2, _ = run_batched(mats, path="persistent", flags=bsvd.FLAG_SPLIT_LARGE, compute_u=False,
+                                    compute_v=False)
+    assert U2 is None and V2 is None and (i2 == 0).all()
+    for i in range(len(mats)):
+        assert np.abs(S2[i] - S[i]).max() <= 50 * min(mats[i].shape) * checks.U32 * S[i][0]
