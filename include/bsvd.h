@@ -108,7 +108,16 @@ typedef struct {
                           QR Factorization"; strided form, native precision): A = Q [R; 0]
                           by Householder QR (of A^H when m < n), the SVD of the
                           min(m, n)-square R by the path `path` selects, U = Q [U_R; 0].
-                          Workspace: bsvd_gesvj_workspace with the same options        */
+                          Workspace: bsvd_gesvj_workspace with the same options;
+                          bit 6: with BSVD_PATH_PERSISTENT on a complex64 pointer-array
+                          batch, the matrices with min(m, n) >= 128 run as one
+                          variable-shape batch on the masked multi-kernel path (same
+                          per-matrix arithmetic as that path on each shape alone), on a
+                          stream the handle owns that is forked from and joined back to
+                          `stream`, beside the persistent launch for the rest; other
+                          types ignore it.  With bit 4 the call returns once those
+                          matrices have converged.  Workspace: bsvd_gesvj_workspace with
+                          the same options                                             */
     int prec;          /* bsvd_prec; MIXED only for d/z and the strided form                 */
     int reserved[5];
 } bsvd_opts;
