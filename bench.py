@@ -48,7 +48,7 @@ PEAK_FP32 = 152 * 128 * 2 * 2.07e9
 # DRAM bytes per matrix of the FP64 fused kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum over a 2,000-matrix launch),
 # valid while the kernel source is unchanged (sha1 prefix below).
-TRAFFIC_PER_MATRIX = {"c72c8ead11ee": 138.7e3}
+TRAFFIC_PER_MATRIX = {"d5114e66119c": 141.6e3}
 KERNEL_SRC = os.path.join(ROOT, "paper_2601_17979_gb300", "csrc", "gesvj_fused.cuh")
 
 
