@@ -334,21 +334,22 @@ def run_uneven(args, rank, world, local):
     # form grouping by shape) -- the path the persistent launch replaces
     # (timed on the first 500 matrices: nearly every shape is distinct, so it
     # runs one launch -- or one multi-kernel sweep loop -- per matrix)
-    sub = {}
-    for x in mats[:min(B, 500)]:
-        sub.setdefault(x.dtype, []).append(torch.from_numpy(np.asfortranarray(x)).to(dev))
-    barrier()
-    a.record(stream)
-    for dt, T in sub.items():
-        bsvd.gesvj_batched(T, path="auto")
-    b.record(stream)
-    barrier()
-    per_shape = a.elapsed_time(b)
-    nsub = sum(len(T) for T in sub.values())
-    line["one_launch_per_shape"] = {"matrices_per_s": nsub / (per_shape * 1e-3), "ms": per_shape,
-                                    "matrices": nsub,
-                                    "distinct_shapes": len({x.shape + (x.dtype,) for x in mats[:nsub]}),
-                                    "persistent_speedup": (per_shape / nsub) / (ms / B)}
+    if not args.no_per_shape:
+        sub = {}
+        for x in mats[:min(B, 500)]:
+            sub.setdefault(x.dtype, []).append(torch.from_numpy(np.asfortranarray(x)).to(dev))
+        barrier()
+        a.record(stream)
+        for dt, T in sub.items():
+            bsvd.gesvj_batched(T, path="auto")
+        b.record(stream)
+        barrier()
+        per_shape = a.elapsed_time(b)
+        nsub = sum(len(T) for T in sub.values())
+        line["one_launch_per_shape"] = {"matrices_per_s": nsub / (per_shape * 1e-3), "ms": per_shape,
+                                        "matrices": nsub,
+                                        "distinct_shapes": len({x.shape + (x.dtype,) for x in mats[:nsub]}),
+                                        "persistent_speedup": (per_shape / nsub) / (ms / B)}
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
         S = min(args.cpu_sample, 400)
@@ -749,6 +750,8 @@ def main():
     ap.add_argument("--sweep-rates", type=float, nargs="*", default=[25, 50, 100, 200])
     ap.add_argument("--sweep-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-per-shape", action="store_true",
+                    help="uneven: skip the one-launch-per-shape comparison (thousands of launches)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
