@@ -63,3 +63,23 @@ def test_single_rank_is_identity():
     assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
     assert bench.sum_over_ranks(2.0, None, "cpu") == 2.0
     assert list(bench.shard(0, 3)) == [0, 1, 2]
+
+
+def test_uneven_launch_count():
+    """The uneven step's launch claim: one persistent launch per type, and
+    for the complex64 split (min(m, n) >= 128) the multi-kernel batch's load,
+    4 * ceil(max sweeps / 4) sweeps of 3 (L_max - 1) + 1 kernels and three
+    finalisation kernels."""
+    from types import SimpleNamespace
+    f32, c64 = np.dtype(np.float32), np.dtype(np.complex64)
+    groups = {f32: [np.zeros((300, 200), np.float32)],
+              c64: [np.zeros((40, 30), np.complex64), np.zeros((512, 300), np.complex64),
+                    np.zeros((200, 130), np.complex64)]}
+    res = {f32: SimpleNamespace(sweeps=torch.tensor([12])),
+           c64: SimpleNamespace(sweeps=torch.tensor([20, 13, 9]))}
+    # complex64 split: n up to 300 -> l = 19 blocks, L = 20; 13 sweeps -> 16 issued
+    per_step = 2 + 1 + 16 * (3 * 19 + 1) + 3
+    assert bench.uneven_launches(groups, res, steps=1) == per_step
+    assert bench.uneven_launches(groups, res, steps=3) == 3 * per_step
+    res_small = {f32: res[f32], c64: SimpleNamespace(sweeps=torch.tensor([20]))}
+    assert bench.uneven_launches({f32: groups[f32], c64: groups[c64][:1]}, res_small, steps=2) == 4
