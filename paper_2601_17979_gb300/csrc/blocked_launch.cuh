@@ -64,7 +64,7 @@ cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stag
     const int heevj_smem = 2 * TWO * LDG * (int)sizeof(T) + InnerTables<T, NB>::bytes();
     const int fin_smem = (kBlkThreads / 32) * (int)sizeof(R) + 16 + 2 * (int)sizeof(T) +
                          a.N * ((int)sizeof(R) + 4) + 16;
-    const int upd_smem = TWO * TWO * (int)sizeof(T);
+    const int upd_smem = TWO * (TWO + 1) * (int)sizeof(T);   // J, column stride up to 2nb + 1
     if ((e = allow_dynamic_smem<blk_heevj<T, NB, GT>>()) != cudaSuccess ||
         (e = allow_dynamic_smem<blk_finalize<T>>()) != cudaSuccess ||
         (e = allow_dynamic_smem<blk_update_fused<T, NB>>()) != cudaSuccess ||

@@ -15,6 +15,8 @@
 // The same kernels serve any matrix too large for the on-chip fused path.
 #pragma once
 
+#include <type_traits>
+
 #include "blocked_layout.h"
 #include "jacobi_common.cuh"
 
@@ -307,6 +309,59 @@ __global__ void __launch_bounds__(kUpdRows) blk_update_fused(const BlockedArgs a
     const int rows = sh.M + sh.N;
     if (blockIdx.z * kUpdRows >= rows) return;
     const T* Jg = static_cast<const T*>(a.J) + sh.oJ + (long long)q * TWO * TWO;
+    if constexpr (std::is_same<T, float2>::value && NB <= 16) {
+        // complex64: 4 rows x 2nb/4 columns per thread.  The four lanes of a
+        // quad share 4 rows (rs, rs + 32, ...) and take columns cg, cg + 4,
+        // ...; J is kept with column stride 2nb + 1 so the quad's reads hit
+        // different banks.  A quarter of a J read per multiply-add instead of
+        // one; each output still sums k in order, the bits of the generic
+        // branch below.
+        constexpr int LDJ = TWO + 1, CJ = TWO / 4, RS = kUpdRows / 4;
+        for (int e = tid; e < TWO * TWO; e += kUpdRows) Js[(e % TWO) + (e / TWO) * LDJ] = Jg[e];
+        __syncthreads();
+        const int cg = tid & 3, rs = tid >> 2;
+        for (int base = blockIdx.z * kUpdRows; base < rows; base += gridDim.z * kUpdRows) {
+            T* X[4];
+            long long ldx[4];
+            bool ok[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int row = base + rs + RS * i;
+                ok[i] = row < rows;
+                ldx[i] = 0;
+                X[i] = ok[i] ? blk_row<T>(a, sh, row, ldx[i]) : nullptr;
+            }
+            T acc[4][CJ];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < CJ; ++j) acc[i][j] = make_s<T>(0);
+#pragma unroll 4
+            for (int k = 0; k < TWO; ++k) {
+                const long long ck = k < NB ? bi * NB + k : bj * NB + k - NB;
+                T xk[4], jk[CJ];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) xk[i] = ok[i] ? X[i][ck * ldx[i]] : make_s<T>(0);
+#pragma unroll
+                for (int j = 0; j < CJ; ++j) jk[j] = Js[k + (cg + 4 * j) * LDJ];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < CJ; ++j) acc[i][j] = fma_s(xk[i], jk[j], acc[i][j]);
+            }
+            __syncwarp();   // the quad has read its rows before any of it writes them
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (ok[i]) {
+#pragma unroll
+                    for (int j = 0; j < CJ; ++j) {
+                        const int c = cg + 4 * j;
+                        X[i][(long long)(c < NB ? bi * NB + c : bj * NB + c - NB) * ldx[i]] = acc[i][j];
+                    }
+                }
+        }
+        return;
+    }
     for (int e = tid; e < TWO * TWO; e += kUpdRows) Js[e] = Jg[e];
     __syncthreads();
     for (int row = blockIdx.z * kUpdRows + tid; row < rows; row += gridDim.z * kUpdRows) {
