@@ -12,7 +12,6 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
-#include <mutex>
 
 #include "bsvd.h"
 
@@ -22,30 +21,25 @@ namespace {
 // on the multi-kernel path, so this holds batches of up to 203 such
 // matrices; larger batches are rejected with BSVD_ERR_WORKSPACE.
 constexpr size_t kStaticScratchBytes = size_t(32) << 20;   // 32 MiB
-constexpr int kMaxDevices = 64;
-
-std::mutex g_setup_mutex;
-void* g_scratch_addr[kMaxDevices] = {};   // device address of the array, per device
 
 }  // namespace
 
 static __device__ __align__(256) unsigned char g_bsvd_static_scratch[kStaticScratchBytes];
 
 // The array's name in host code is only a host-side stand-in: its device
-// address has to be looked up, once per device, with that device current.
+// address is looked up with the calling thread's device current.  It is
+// looked up on every call, not cached: after cudaDeviceReset, or in another
+// context, the module is loaded again and the address may change, and a
+// cached pointer would then point at memory this call does not own.  The
+// lookup may load the module on a device's first call, so that first call
+// should come before any stream capture.
 static bsvd_status static_scratch(void** ptr) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return BSVD_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_bsvd_static_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return BSVD_ERR_CUDA;
-        }
-        g_scratch_addr[dev] = p;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_bsvd_static_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return BSVD_ERR_CUDA;
     }
-    *ptr = g_scratch_addr[dev];
+    *ptr = p;
     return BSVD_OK;
 }
 

@@ -92,6 +92,31 @@ def test_noalloc_matches_regular_entry_point_twice(lib):
             assert checks.violations(meas, U) == [], (call, b, meas)
 
 
+def test_noalloc_stale_scratch_from_a_different_call(lib):
+    """A first call leaves the array in another state (a larger batch stopped
+    after one sweep, so its status words and pair flags are still set); the
+    next, smaller call must start from scratch: converged, and sigma within
+    50 n u of the FP64 oracle, residual and orthogonality within their bounds."""
+    import oracle
+    big = synth.uniform_batch("tall128x64_f64", 150, start=2000)
+    Ab = torch.from_numpy(big.transpose(0, 2, 1).copy()).cuda()
+    out = outputs(150)
+    assert call_noalloc(lib, Ab, out, binding.make_opts(nb=16, max_sweeps=1, path="blocked")) == 0
+    torch.cuda.synchronize()
+    assert (out[3].cpu().numpy() == 1).all()        # not converged after 1 sweep: info = 1
+    mats = synth.uniform_batch("tall128x64_f64", 24, start=3000)
+    At = torch.from_numpy(mats.transpose(0, 2, 1).copy()).cuda()
+    got = outputs(24)
+    assert call_noalloc(lib, At, got, binding.make_opts(nb=16, path="blocked")) == 0
+    torch.cuda.synchronize()
+    S1, U1, V1, i1, w1 = host(got)
+    assert (i1 == 0).all(), i1
+    ref = oracle.gesvj(list(mats), tol=30 * U)
+    for b in range(24):
+        meas = checks.measures(mats[b], S1[b], U1[b], V1[b], ref["S"][b])
+        assert checks.violations(meas, U) == [], (b, meas)
+
+
 def test_noalloc_rejects_batches_beyond_capacity(lib):
     B = 204                                          # needs more than the 32 MiB array
     At = torch.zeros((B, N, M), dtype=torch.float64, device="cuda")
