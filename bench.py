@@ -721,7 +721,7 @@ def tallskinny_flops(m, n, sweeps, qr):
 SQ32_STEPS = 100
 
 # Mixed-precision variants timed beside the default (name, flags).
-MIXED_VARIANTS = []
+MIXED_VARIANTS = [("mixed_fp64_angles", 256), ("mixed_ffma", 128)]
 
 
 def run_square32(args, rank, world, local):
@@ -1221,6 +1221,11 @@ def main():
     # The paper's baseline path on the same FP64 batch ("vs plain FP64 Jacobi"):
     # multi-kernel, inner eigensolver to convergence, two-stage update, no masks.
     variants = [("fp64_mixed", dict(prec="mixed"))] if not args.no_mixed else []
+    if not args.no_mixed and not args.no_variants:
+        # the FP32 sweeps with FP64 rotations and pair test (flags bit 8), and
+        # with the Gram and update on the FMA pipes instead of the tensor cores
+        variants += [("fp64_mixed_fp64_angles", dict(prec="mixed", flags=256)),
+                     ("fp64_mixed_ffma", dict(prec="mixed", flags=128))]
     if not args.no_plain:
         variants.append(("plain_fp64", dict(path="plain")))
     if args.ladder:
@@ -1245,6 +1250,23 @@ def main():
                                                                         ref64, U64),
                       "clocks": v_sampler.summary()}
         del work
+
+    # the FP32 batch with the Gram and update on the FMA pipes (flags bit 7)
+    # instead of the tensor cores, for comparison
+    if not args.no_variants:
+        barrier()
+        f_sampler = ClockSampler(gpu_uuid(torch, dev))
+        with f_sampler:
+            ts = timed_calls(torch, lambda: bsvd.gesvj(A32, nb=NB, tol=TOL_K * U32, out=o32, flags=128),
+                             max(5, min(args.steps, 10)), stream, warmup=1)
+        f_ms = statistics.median(ts)
+        sw = o32[4].cpu().numpy()
+        line["fp32_ffma"] = {"matrices_per_s": B / (f_ms * 1e-3), "ms": f_ms, "sweeps_mean": float(sw.mean()),
+                             "tensor_core_ms_over_this": t32 * 1e3 / f_ms,
+                             "info_nonzero": int((o32[3].cpu().numpy() != 0).sum()),
+                             "accuracy_worst_over_bound": accuracy_over_bounds(
+                                 [A32h[i] for i in samp], *sampled(o32), ref32, U32),
+                             "clocks": f_sampler.summary()}
 
     # CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu:

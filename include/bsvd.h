@@ -99,11 +99,15 @@ typedef struct {
                           batch convergence).  Bits 1-2 with AUTO select the multi-kernel
                           path.
                           bit 3: no CUDA graph (the masked multi-kernel path otherwise
-                          records one sweep into a graph and replays it each sweep);
-                          bit 4: the masked multi-kernel path reads the batch's
-                          convergence on the host every 4 sweeps and launches no more
-                          sweeps once every matrix has converged (the call then
-                          synchronises `stream`; results are unchanged);
+                          runs its sweeps as one graph whose conditional WHILE node
+                          repeats one recorded sweep until no matrix is active or
+                          max_sweeps sweeps have run, decided on the device; without
+                          graphs it launches max_sweeps sweeps);
+                          bit 4: without the device-side loop (graphs off, or a driver
+                          without conditional graph nodes) the masked multi-kernel path
+                          reads the batch's convergence on the host every 4 sweeps and
+                          launches no more sweeps once every matrix has converged (the
+                          call then synchronises `stream`; results are unchanged);
                           bit 5: QR pre-processing (Sec. "Pre-processing the SVD using a
                           QR Factorization"; strided form, native precision): A = Q [R; 0]
                           by Householder QR (of A^H when m < n), the SVD of the
@@ -117,7 +121,13 @@ typedef struct {
                           `stream`, beside the persistent launch for the rest; other
                           types ignore it.  With bit 4 the call returns once those
                           matrices have converged.  Workspace: bsvd_gesvj_workspace with
-                          the same options                                             */
+                          the same options;
+                          bit 7: real FP32 with nb = 8 or 16 forms the Gram blocks and
+                          the rotation updates on the FMA pipes (register tiles)
+                          instead of the tensor cores (split-TF32 mma, FP32 accuracy);
+                          bit 8: single-precision data (and the FP32 sweeps of MIXED)
+                          take the pair test and the rotation (Eq. sin-cos) in FP64,
+                          rounded once to FP32                                         */
     int prec;          /* bsvd_prec; MIXED only for d/z and the strided form                 */
     int reserved[5];
 } bsvd_opts;
@@ -230,10 +240,12 @@ bsvd_status bsvd_autotune(bsvd_handle handle, char dtype, bsvd_job jobu, bsvd_jo
  * (PLAIN if opts->path asks for it, BLOCKED otherwise) with its workspace in a
  * static 32 MiB device array that every GPU loading the library holds until
  * exit.  A batch whose workspace exceeds 32 MiB (more than 203 matrices of
- * 128 x 64) returns BSVD_ERR_WORKSPACE and launches nothing.  The first call
- * on each device looks up the array's device address with that device
- * current; make that first call before any stream capture.  All calls share
- * the array, so calls that overlap on the GPU race: serialise them.
+ * 128 x 64) returns BSVD_ERR_WORKSPACE and launches nothing.  Every call
+ * looks up the array's device address with the calling thread's device
+ * current (so a cudaDeviceReset leaves no stale address behind); the first
+ * call on a device may load the module, so make it before any stream
+ * capture.  All calls share the array, so calls that overlap on the GPU
+ * race: serialise them.
  */
 bsvd_status bsvd_dgesvj_strided_noalloc(bsvd_handle handle, bsvd_job jobu, bsvd_job jobv, int batch,
                                         int m, int n, const double* dA, int lda, long long strideA,

@@ -26,6 +26,7 @@ PATHS = {"auto": 0, "fused": 1, "plain": 2, "blocked": 3, "persistent": 4}
 PATH_NAMES = {v: k for k, v in PATHS.items()}
 FLAG_NO_V_CORRECTION, FLAG_TWO_STAGE, FLAG_NO_MASKS, FLAG_NO_GRAPH, FLAG_SYNC_CHECK, FLAG_QR = 1, 2, 4, 8, 16, 32
 FLAG_SPLIT_LARGE = 64
+FLAG_F32_FFMA, FLAG_WIDE_ANGLES = 128, 256
 DTYPES = {torch.float32: "s", torch.float64: "d", torch.complex64: "c", torch.complex128: "z"}
 REAL = {torch.float32: torch.float32, torch.float64: torch.float64,
         torch.complex64: torch.float32, torch.complex128: torch.float64}

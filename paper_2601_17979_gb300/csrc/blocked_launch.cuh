@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <cstring>
 #include <type_traits>
 
 #include "blocked_layout.h"
@@ -11,6 +12,67 @@
 #include "internal.h"
 
 namespace bsvd {
+
+// End of a sweep inside the device-side sweep loop: count the sweep and keep
+// looping while some matrix is still active and fewer than max_sweeps sweeps
+// have run.  The count starts at zero each launch (the host clears it), and
+// a negative value is read as zero, so the loop ends after at most
+// max_sweeps sweeps whatever the counter held.
+static __global__ void blk_continue(cudaGraphConditionalHandle h, const BlockedArgs a) {
+    int* counter = a.any_active + 1;
+    const int c = max(*counter, 0) + 1;
+    *counter = c;
+    cudaGraphSetConditional(h, (*a.any_active != 0 && c < a.max_sweeps) ? 1u : 0u);
+}
+
+// The masked sweep loop as one CUDA graph: a conditional WHILE node whose
+// body is one sweep (every round's launches, the convergence kernel) plus
+// blk_continue, which stops the loop on the device once no matrix is
+// active.  No sweep is issued after the batch has converged and the host
+// never waits.  Returns cudaErrorNotSupported, having queued nothing, when
+// the graph cannot be built (the caller then replays a plain one-sweep
+// graph max_sweeps times).
+template <class Sweep>
+cudaError_t blk_run_while(const BlockedArgs& a, cudaStream_t st, cudaStream_t capture, Sweep& sweep) {
+    if (a.max_sweeps < 1) return cudaErrorNotSupported;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle h;
+    cudaGraphNode_t node;
+    bool ok = cudaGraphCreate(&g, 0) == cudaSuccess &&
+              cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault) == cudaSuccess;
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    ok = ok && cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess;
+    if (ok) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        if (cudaStreamBeginCaptureToGraph(capture, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+            cudaSuccess) {
+            cudaError_t ce = sweep(capture);
+            if (ce == cudaSuccess) {
+                blk_continue<<<1, 1, 0, capture>>>(h, a);
+                ce = cudaGetLastError();
+            }
+            cudaGraph_t out = nullptr;
+            const cudaError_t ee = cudaStreamEndCapture(capture, &out);
+            ok = ce == cudaSuccess && ee == cudaSuccess && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+        } else {
+            ok = false;
+        }
+    }
+    cudaError_t e = cudaErrorNotSupported;
+    if (ok) {
+        e = cudaMemsetAsync(a.any_active + 1, 0, sizeof(int), st);   // the sweep counter
+        if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+    } else {
+        cudaGetLastError();
+    }
+    if (exec) cudaGraphExecDestroy(exec);   // freed once the queued launch finishes
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
 
 template <int NB> struct BlkCfg;
 template <> struct BlkCfg<4>  { static constexpr int GT = 32; };
@@ -64,7 +126,9 @@ cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stag
     const int heevj_smem = 2 * TWO * LDG * (int)sizeof(T) + InnerTables<T, NB>::bytes();
     const int fin_smem = (kBlkThreads / 32) * (int)sizeof(R) + 16 + 2 * (int)sizeof(T) +
                          a.N * ((int)sizeof(R) + 4) + 16;
-    const int upd_smem = TWO * (TWO + 1) * (int)sizeof(T);   // J, column stride up to 2nb + 1
+    // J, column stride up to 2nb + 1; real FP32 J's split-TF32 fragments
+    const int upd_smem = std::max(TWO * (TWO + 1) * (int)sizeof(T),
+                                  std::is_same<T, float>::value ? j_fragment_bytes<NB>() : 0);
     if ((e = allow_dynamic_smem<blk_heevj<T, NB, GT>>()) != cudaSuccess ||
         (e = allow_dynamic_smem<blk_finalize<T>>()) != cudaSuccess ||
         (e = allow_dynamic_smem<blk_update_fused<T, NB>>()) != cudaSuccess ||
@@ -89,7 +153,11 @@ cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stag
     // one sweep: every round's stages, then the end-of-sweep bookkeeping
     auto sweep = [&](cudaStream_t s) -> cudaError_t {
         for (int r = 0; r < a.L - 1; ++r) {
-            if constexpr (std::is_same<T, float>::value && NB >= 8)
+            // real FP32: the tensor cores (flags bit 7: FMA register tiles)
+            if constexpr (std::is_same<T, float>::value && (NB == 8 || NB == 16)) {
+                if (a.flags & 128) blk_gram_f32<NB><<<gpair, kBlkThreads, 0, s>>>(a, r);
+                else blk_gram_f32_tc<NB><<<gpair, kBlkThreads, 0, s>>>(a, r);
+            } else if constexpr (std::is_same<T, float>::value && NB >= 8)
                 blk_gram_f32<NB><<<gpair, kBlkThreads, 0, s>>>(a, r);
             else
                 blk_gram<T, NB><<<gpair, kBlkThreads, 0, s>>>(a, r);
@@ -116,6 +184,9 @@ cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stag
             if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
             if (!any) break;
         }
+    } else if (capture && (e = blk_run_while(a, st, capture, sweep)) != cudaErrorNotSupported) {
+        // the sweep loop ran (or failed) as one graph with a device-side loop
+        if (e != cudaSuccess) return e;
     } else {
         // masked: converged matrices skip every stage, so max_sweeps sweeps are
         // issued without a host round trip; one sweep is recorded once into a

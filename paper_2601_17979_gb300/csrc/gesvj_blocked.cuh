@@ -19,6 +19,7 @@
 
 #include "blocked_layout.h"
 #include "jacobi_common.cuh"
+#include "tc_f32.cuh"
 
 namespace bsvd {
 
@@ -125,6 +126,66 @@ __global__ void __launch_bounds__(kBlkThreads) blk_gram_f32(const BlockedArgs a,
                 G[cc + rr * TWO] = acc[i][j];
             }
     }
+}
+
+// ---- S2, real FP32 on the tensor cores (nb = 8, 16) -------------------------------
+// The same 64-row chunks staged in shared memory; the 16 x 16 blocks of the
+// Gram block formed by split-TF32 mma tiles (tc_f32.cuh).  The eight warps
+// split each chunk's eight k-steps: nb = 16 has four blocks, two warps a
+// block; nb = 8 one block, all eight warps.  The warps' partial blocks are
+// summed in warp order (a fixed order: the bits do not depend on timing),
+// and the upper entries written and mirrored.
+template <int NB>
+__global__ void __launch_bounds__(kBlkThreads) blk_gram_f32_tc(const BlockedArgs a, int r) {
+    constexpr int TWO = 2 * NB, NT = kBlkThreads, NW = NT / 32, NBLK = TWO / 16, NB2 = NBLK * NBLK;
+    constexpr int WPB = NW / NB2;                       // warps per block
+    static_assert(NW % NB2 == 0, "warps per Gram block");
+    constexpr int KC = kGramChunk, KP = KC + 4;
+    __shared__ __align__(16) float P[KP * TWO];
+    __shared__ float red[NW * 32 * 8];
+    const int b = blockIdx.x, q = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (blk_skip(a, b)) return;
+    const BlkShape sh = blk_shape(a, b);
+    int bi, bj;
+    if (!blk_pair(sh, r, q, bi, bj)) return;
+    const float* W = static_cast<const float*>(a.W) + sh.oW;
+    const int M = sh.M;
+    const int blk = warp % NB2, sub = warp / NB2, bm = blk / NBLK, bn = blk % NBLK;
+    float acc[2][4];
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
+    for (int k0 = 0; k0 < M; k0 += KC) {
+        const int kc = min(KC, M - k0);
+        for (int e = tid; e < KC * TWO; e += NT) {
+            const int kk = e % KC, c = e / KC;
+            const int col = c < NB ? bi * NB + c : bj * NB + (c - NB);
+            P[kk + c * KP] = kk < kc ? W[k0 + kk + (long long)col * M] : 0.f;   // zero tail: adds nothing
+        }
+        __syncthreads();
+        gram_block_acc<NB>(P, KP, kc, 0, NB, bm, bn, sub, WPB, lane, acc);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) red[(warp * 32 + lane) * 8 + 4 * j + i] = acc[j][i];
+    __syncthreads();
+    if (sub != 0) return;
+    float* G = static_cast<float*>(a.G) + sh.oG + (long long)q * TWO * TWO;
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float x = red[(blk * 32 + lane) * 8 + 4 * j + i];
+            for (int s2 = 1; s2 < WPB; ++s2) x += red[((blk + s2 * NB2) * 32 + lane) * 8 + 4 * j + i];
+            const int rr = 16 * bm + g + 8 * (i >> 1), cc = 16 * bn + 8 * j + 2 * t + (i & 1);
+            if (rr > cc) continue;                          // lower entries: the mirror of an upper one
+            G[rr + cc * TWO] = x;
+            G[cc + rr * TWO] = x;
+        }
 }
 
 template <class T>
@@ -273,7 +334,8 @@ __global__ void __launch_bounds__(GT) blk_heevj(const BlockedArgs a, int r) {
         G[j + i * LDG] = conj_s(g);
     }
     __syncthreads();
-    const int seen = inner_jacobi<T, NB, GT>(G, J, tb, (Real<T>)a.tol, a.inner_sweeps, tid, 1);
+    const int seen = inner_jacobi<T, NB, GT>(G, J, tb, (Real<T>)a.tol, a.inner_sweeps, tid, 1, NoBackground(),
+                                             nullptr, (a.flags & 256) != 0);
     T* Jg = static_cast<T*>(a.J) + sh.oJ + (long long)q * TWO * TWO;
     for (int e = tid; e < TWO * TWO; e += GT) Jg[(e % TWO) + (e / TWO) * TWO] = J[(e % TWO) + (e / TWO) * LDG];
     if (tid == 0) {
@@ -309,6 +371,24 @@ __global__ void __launch_bounds__(kUpdRows) blk_update_fused(const BlockedArgs a
     const int rows = sh.M + sh.N;
     if (blockIdx.z * kUpdRows >= rows) return;
     const T* Jg = static_cast<const T*>(a.J) + sh.oJ + (long long)q * TWO * TWO;
+    if constexpr (std::is_same<T, float>::value && (NB == 8 || NB == 16))
+      if (!(a.flags & 128)) {
+        // real FP32: 16-row tiles of W, then of V, on the tensor cores
+        // (split TF32, tc_f32.cuh); a CTA's four warps take the tiles of its
+        // row blocks, eight tiles a block
+        uint4* Jf = reinterpret_cast<uint4*>(smem_js);
+        j_fragments<NB, kUpdRows, TWO>(Jg, Jf, tid);
+        __syncthreads();
+        const int tw = (sh.M + 15) / 16, tt = tw + (sh.N + 15) / 16, warp = tid >> 5, lane = tid & 31;
+        float* Wm = static_cast<float*>(a.W) + sh.oW;
+        float* Vm = static_cast<float*>(a.Vw) + sh.oV;
+        for (int base = blockIdx.z * (kUpdRows / 16); base < tt; base += gridDim.z * (kUpdRows / 16))
+            for (int tile = base + warp; tile < min(tt, base + kUpdRows / 16); tile += kUpdRows / 32) {
+                if (tile < tw) update_rows_mma<NB>(Wm, sh.M, sh.M, 16 * tile, bi * NB, bj * NB, Jf, lane);
+                else           update_rows_mma<NB>(Vm, sh.N, sh.N, 16 * (tile - tw), bi * NB, bj * NB, Jf, lane);
+            }
+        return;
+    }
     if constexpr (std::is_same<T, float2>::value && NB <= 16) {
         // complex64: 4 rows x 2nb/4 columns per thread.  The four lanes of a
         // quad share 4 rows (rs, rs + 32, ...) and take columns cg, cg + 4,

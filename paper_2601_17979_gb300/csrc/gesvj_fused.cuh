@@ -22,6 +22,7 @@
 
 #include "fused_f32.cuh"
 #include "jacobi_common.cuh"
+#include "tc_f32.cuh"
 
 namespace bsvd {
 
@@ -48,7 +49,10 @@ struct FusedArgs {
     int wantU, wantV;
 };
 
-enum : int { kFlagNoVCorrection = 1 };
+// bsvd_opts.flags bits read by the kernels: 0 no Newton-Schulz step on V;
+// 7 real FP32 Gram and update on the FMA pipes (register tiles) instead of
+// the tensor cores; 8 single-precision rotations and pair test in FP64.
+enum : int { kFlagNoVCorrection = 1, kFlagF32Ffma = 128, kFlagWideAngles = 256 };
 
 // Shared-memory bytes of one thread group's scratch (G, J, rotation table).
 // Working shape and leading dimensions of one matrix: M >= N (A^H when
@@ -71,6 +75,7 @@ __host__ __device__ inline void fused_dims(int m, int n, FusedArgs& a) {
         a.ldw = (M + 3) & ~3;
         if (a.ldw % 8 == 0) a.ldw += 4;
         a.ldvs = (N + 3) & ~3;
+        if (a.ldvs % 8 == 0) a.ldvs += 4;
     } else {
         a.ldw = M | 1;
         a.ldvs = N | 1;
@@ -87,12 +92,14 @@ __host__ __device__ inline long long fused_slot_elems(const FusedArgs& a) {
     return w + (long long)a.ldvs * a.Np;
 }
 
-// FP32 adds J^T (2nb x 2nb, 16-byte aligned) for the tiled update; the other
-// types a second J (the previous pair's, for the deferred V update).
+// FP32 adds J as split-TF32 fragments for the tensor-core update (nb >= 8:
+// 8 (2nb)^2 bytes) or J^T for the FFMA-tiled update (nb = 4), 16-byte
+// aligned; the other types a second J (the previous pair's, for the
+// deferred V update).
 template <class T, int NB>
 __host__ __device__ constexpr int fused_group_bytes() {
     return ((2 * (2 * NB) * (2 * NB + 1) * (int)sizeof(T) + InnerTables<T, NB>::bytes() + 15) & ~15) +
-           (std::is_same<T, float>::value ? (2 * NB) * (2 * NB) * 4
+           (std::is_same<T, float>::value ? (NB >= 8 ? 8 * (2 * NB) * (2 * NB) : (2 * NB) * (2 * NB) * 4)
                                           : (((2 * NB) * (2 * NB + 1) * (int)sizeof(T) + 15) & ~15));
 }
 
@@ -260,9 +267,11 @@ __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T
                 // S2: G = P^H P, upper triangle, mirrored to keep G Hermitian.
                 // Lanes l and l+16 of a warp sum the same entry over the two
                 // halves of the rows [0, M/2) and [M/2, M); one shuffle adds them.
-                // FP32: register-tiled (fused_f32.cuh).
+                // FP32: split-TF32 tensor-core tiles (tc_f32.cuh), or
+                // FFMA register tiles for nb = 4 (fused_f32.cuh).
                 if constexpr (std::is_same<T, float>::value) {
-                    gram_f32_tiled<NB, GT>(W, ldw, M, bi * NB, bj * NB, G, gt);
+                    if (NB >= 8 && !(a.flags & kFlagF32Ffma)) gram_f32_mma<NB < 8 ? 8 : NB, GT>(W, ldw, M, bi * NB, bj * NB, G, gt);
+                    else gram_f32_tiled<NB, GT>(W, ldw, M, bi * NB, bj * NB, G, gt);
                 } else if constexpr (!OnChip) {
                     // W in global memory: 2 x 2 tiles of upper entries per lane
                     // pair, four independent sums (half the loads per FMA of
@@ -342,7 +351,8 @@ __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T
                 stepped = true;
                 if constexpr (kDefer) {
                     int ns = 0;
-                    seen = inner_jacobi<T, NB, GT>(G, J, tb, tol, a.inner_sweeps, gt, g + 1, dv, &ns);
+                    seen = inner_jacobi<T, NB, GT>(G, J, tb, tol, a.inner_sweeps, gt, g + 1, dv, &ns,
+                                                   (a.flags & kFlagWideAngles) != 0);
                     if (dv.J) {   // the deferred V rows the background warps did not reach
                         for (int wt = ns * inner_background_warps<GT>() + (gt >> 5); wt < dv.tasks(); wt += GT / 32)
                             dv(wt);
@@ -350,7 +360,8 @@ __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T
                     }
                     group_sync(g, GT);
                 } else {
-                    seen = inner_jacobi<T, NB, GT>(G, J, tb, tol, a.inner_sweeps, gt, g + 1);
+                    seen = inner_jacobi<T, NB, GT>(G, J, tb, tol, a.inner_sweeps, gt, g + 1, NoBackground(), nullptr,
+                                                   (a.flags & kFlagWideAngles) != 0);
                 }
                 if (seen == 0) break;                       // J = I: pair masked (Design-4)
                 if (gt == 0) swflag[sw] = 1;
@@ -360,9 +371,17 @@ __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T
                 // l and write the first and the second nb outputs of it, so the
                 // M + n rows spread evenly over the group.  FP32: register tiles.
                 if constexpr (std::is_same<T, float>::value) {
-                    for (int e = gt; e < TWO * TWO; e += GT) Jt[(e / TWO) + (e % TWO) * TWO] = J[(e % TWO) + (e / TWO) * LDG];
-                    group_sync(g, GT);
-                    update_f32_tiled<NB, GT, 2>(W, ldw, ldw, Vs, ldvs, needVs ? ldvs : 0, bi * NB, bj * NB, Jt, gt, g + 1);
+                    if (NB >= 8 && !(a.flags & kFlagF32Ffma)) {
+                        constexpr int NBT = NB < 8 ? 8 : NB;       // (nb = 4 never takes this branch)
+                        uint4* Jf = reinterpret_cast<uint4*>(gb_tail);
+                        j_fragments<NBT, GT>(J, Jf, gt);
+                        group_sync(g, GT);
+                        update_f32_mma<NBT, GT>(W, ldw, M, Vs, ldvs, needVs ? N : 0, bi * NB, bj * NB, Jf, gt);
+                    } else {
+                        for (int e = gt; e < TWO * TWO; e += GT) Jt[(e / TWO) + (e % TWO) * TWO] = J[(e % TWO) + (e / TWO) * LDG];
+                        group_sync(g, GT);
+                        update_f32_tiled<NB, GT, 2>(W, ldw, ldw, Vs, ldvs, needVs ? ldvs : 0, bi * NB, bj * NB, Jt, gt, g + 1);
+                    }
                 } else if constexpr (std::is_same<T, float2>::value) {
                     // complex64: 4 rows x 2nb/8 columns per lane (columns
                     // cg, cg + 8, ...: conflict-free J reads with its padded

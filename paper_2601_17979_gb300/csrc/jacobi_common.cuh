@@ -3,6 +3,8 @@
 // reductions, and the inner Jacobi eigensolver on a 2nb x 2nb Gram block.
 #pragma once
 
+#include <type_traits>
+
 #include "scalar.cuh"
 
 namespace bsvd {
@@ -136,16 +138,58 @@ __device__ __forceinline__ double rotation_tan(double x, double y) {
     return (x >= 0 ? y : -y) / (fabs(x) + hypot(x, y));
 }
 
+// FP64 counterparts of the single-precision types, for rotations computed in
+// FP64 from FP32 Gram entries (the mixed-precision option).
+template <class T> struct WideOf { using type = T; };
+template <> struct WideOf<float> { using type = double; };
+template <> struct WideOf<float2> { using type = double2; };
+__device__ __forceinline__ double to_wide(float x) { return (double)x; }
+__device__ __forceinline__ double2 to_wide(float2 x) { return make_double2((double)x.x, (double)x.y); }
+__device__ __forceinline__ float to_narrow(double x) { return __double2float_rn(x); }
+__device__ __forceinline__ float2 to_narrow(double2 x) { return make_float2(__double2float_rn(x.x), __double2float_rn(x.y)); }
+
+// The rotation of inner_rotation with the pair test and Eq. (sin-cos)
+// evaluated in FP64 on the single-precision Gram entries (exactly widened),
+// c, t and e s rounded once to the working precision at the end.
+template <class T, int NB>
+__device__ __forceinline__ int inner_rotation_wide(const T* G, Real<T> tol, int p, int q, int slot,
+                                                   typename InnerTables<T, NB>::Slot* out) {
+    using R = Real<T>;
+    using TW = typename WideOf<T>::type;
+    using RW = Real<TW>;
+    constexpr int LDG = 2 * NB + 1;
+    const RW gpp = (RW)re(G[p + p * LDG]), gqq = (RW)re(G[q + q * LDG]);
+    const TW gpq = to_wide(G[p + q * LDG]);
+    const RW apq = abs_s(gpq), tw = (RW)tol;
+    // squares of widened single-precision values stay inside FP64's range
+    const bool fire = gpp > 0 && gqq > 0 && apq > 0 && apq * apq >= (tw * tw) * (gpp * gqq);
+    RW c = 1, t = 0;
+    TW es = make_s<TW>(0);
+    if (fire) {
+        t = rotation_tan(gpp - gqq, 2 * apq);
+        c = 1.0 / sqrt(fma(t, t, 1.0));
+        es = scale(phase_s(gpq, apq), t * c);
+    }
+    typename InnerTables<T, NB>::Slot rec;
+    rec.c = (R)c; rec.t = (R)t; rec.es = to_narrow(es);
+    rec.pqf = p | (q << 8) | ((fire ? 1 : 0) << 16);
+    out[slot] = rec;
+    return fire;
+}
+
 // One thread's rotation for slot `slot` of round-robin step `st` on the 2NB
 // indices: test |g_pq| >= tol sqrt(g_pp) sqrt(g_qq) (Alg. 1) and form
 // (c, s, e^{i phi}) by Eq. (sin-cos) with sign(0) = +1.  Returns fired.
+// `wide` (single precision only): test and rotation in FP64.
 template <class T, int NB>
 __device__ __forceinline__ int inner_rotation(const T* G, Real<T> tol, int st, int slot,
-                                              typename InnerTables<T, NB>::Slot* out) {
+                                              typename InnerTables<T, NB>::Slot* out, bool wide = false) {
     using R = Real<T>;
     constexpr int TWO = 2 * NB, LDG = TWO + 1;
     int p, q;
     rr_pair(TWO, st, slot, p, q);
+    if constexpr (!std::is_same<T, typename WideOf<T>::type>::value)
+        if (wide) return inner_rotation_wide<T, NB>(G, tol, p, q, slot, out);
     const R gpp = re(G[p + p * LDG]), gqq = re(G[q + q * LDG]);
     const T gpq = G[p + q * LDG];
     const R apq = abs_s(gpq);
@@ -194,7 +238,7 @@ __host__ __device__ constexpr int inner_background_warps() { return GT > 32 ? GT
 
 template <class T, int NB, int GT, class Bg = NoBackground>
 __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> tol, int sweeps,
-                            int gt, int bar, const Bg& bg = Bg(), int* nsteps = nullptr) {
+                            int gt, int bar, const Bg& bg = Bg(), int* nsteps = nullptr, bool wide = false) {
     using R = Real<T>;
     constexpr int TWO = 2 * NB, LDG = TWO + 1, STEPS = TWO - 1;
     constexpr int NBLK = NB * (NB + 1) / 2, NBU = (NBLK + GT - 1) / GT;
@@ -212,7 +256,7 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
     if (gt == 0) { tb.count[0] = 0; tb.count[1] = 0; }
     named_sync(bar, GT);
     if (gt < 32) {   // warp 0 forms the rotations; one ballot counts the fired ones
-        const int f = gt < NB ? inner_rotation<T, NB>(G, tol, 0, gt, tb.step(0)) : 0;
+        const int f = gt < NB ? inner_rotation<T, NB>(G, tol, 0, gt, tb.step(0), wide) : 0;
         const unsigned m = __ballot_sync(0xffffffffu, f);
         if (gt == 0) tb.count[0] += __popc(m);
     }
@@ -292,7 +336,7 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
             const bool last = (st + 1 == STEPS);
             if (gt < 32 && !(last && isw + 1 == sweeps)) {
                 const int nisw = last ? isw + 1 : isw;
-                const int f = gt < NB ? inner_rotation<T, NB>(G, tol, last ? 0 : st + 1, gt, tb.step((gs + 1) & 1)) : 0;
+                const int f = gt < NB ? inner_rotation<T, NB>(G, tol, last ? 0 : st + 1, gt, tb.step((gs + 1) & 1), wide) : 0;
                 const unsigned m = __ballot_sync(0xffffffffu, f);
                 if (gt == 0) tb.count[nisw & 1] += __popc(m);
             }

@@ -37,7 +37,7 @@ def test_autotune_picks_a_converging_candidate_and_auto_follows_it():
         assert checks.violations(meas, checks.U32) == [], meas
 
 
-@pytest.mark.parametrize("dtype", [torch.float64, torch.complex64])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.complex64])
 def test_graph_replay_equals_direct_launches(dtype):
     rng = np.random.default_rng(9)
     x = rng.standard_normal((6, 150, 90))
@@ -50,3 +50,19 @@ def test_graph_replay_equals_direct_launches(dtype):
     for a, b in zip(r1, r2):
         assert torch.equal(a, b)
     assert (r1.info == 0).all()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("max_sweeps", [1, 3])
+def test_device_sweep_loop_stops_at_max_sweeps(dtype, max_sweeps):
+    """The graph's device-side sweep loop runs at most max_sweeps sweeps: a
+    batch that needs more ends with info = sweeps = max_sweeps, the same
+    bits as issuing max_sweeps sweeps from the host (graphs off)."""
+    rng = np.random.default_rng(31)
+    A = torch.from_numpy(rng.standard_normal((5, 140, 100))).to(dtype).cuda()
+    r1 = bsvd.gesvj(A, path="blocked", nb=16, max_sweeps=max_sweeps)
+    r2 = bsvd.gesvj(A, path="blocked", nb=16, max_sweeps=max_sweeps, flags=bsvd.FLAG_NO_GRAPH)
+    torch.cuda.synchronize()
+    assert (r1.info == max_sweeps).all() and (r1.sweeps == max_sweeps).all()
+    for a, b in zip(r1, r2):
+        assert torch.equal(a, b)

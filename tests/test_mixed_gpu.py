@@ -82,3 +82,14 @@ def test_mixed_rejected_for_single_precision():
     A = torch.zeros((2, 8, 4), dtype=torch.float32, device="cuda")
     with pytest.raises(bsvd.BsvdError, match="INVALID"):
         bsvd.gesvj(A, prec="mixed")
+
+
+@pytest.mark.parametrize("flags", [bsvd.FLAG_WIDE_ANGLES, bsvd.FLAG_F32_FFMA])
+def test_mixed_variants_meet_fp64_bounds(flags):
+    """Mixed precision with FP64 rotations in the FP32 sweeps (bit 8), and
+    with the FP32 Gram and update on the FMA pipes (bit 7): FP64 bounds."""
+    mats = synth.matrices("tall128x64_f64", range(12)) + [synth.matrix("mixed96", i) for i in (0, 2)]
+    ref = oracle.gesvj(mats, tol=30 * U)
+    for lo, hi in ((0, 12), (12, 14)):
+        S, Uo, Vo, info, sw = run(mats[lo:hi], nb=16, prec="mixed", flags=flags)
+        check(mats[lo:hi], S, Uo, Vo, info, ref["S"][lo:hi], f"flags {flags}")

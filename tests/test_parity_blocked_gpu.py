@@ -171,3 +171,15 @@ def test_host_convergence_check_gives_same_bits(dtype):
     S2, U2, V2, i2, w2 = run_gpu(mats, nb=16, path="blocked", flags=bsvd.FLAG_SYNC_CHECK)
     assert (i1 == 0).all() and np.array_equal(w1, w2)
     assert np.array_equal(S1, S2) and np.array_equal(U1, U2) and np.array_equal(V1, V2)
+
+
+@pytest.mark.parametrize("flags", [0, bsvd.FLAG_F32_FFMA, bsvd.FLAG_WIDE_ANGLES])
+@pytest.mark.parametrize("m,n,nb", [(200, 150, 16), (257, 33, 8), (150, 260, 16)])
+def test_blocked_fp32_tensor_core_and_ffma(flags, m, n, nb):
+    """The multi-kernel FP32 Gram and update on the tensor cores (default),
+    on the FMA tiles (flags bit 7), and with FP64 rotations (bit 8)."""
+    rng = np.random.default_rng(m * 3 + n + nb + flags)
+    mats = [rng.standard_normal((m, n)).astype(np.float32) for _ in range(3)]
+    S, U, V, info, sw = run_gpu(mats, nb=nb, path="blocked", flags=flags)
+    ref = oracle.gesvj(mats)
+    check(mats, S, U, V, info, ref["S"], f"flags {flags} {m}x{n}")

@@ -200,3 +200,38 @@ def test_blocked_oracle_sweep_counts_close():
     ref = oracle.gesvj(mats, nb=8, inner_sweeps=1, tol=tol)
     diff = np.abs(sw - ref["sweeps"])
     assert (diff <= 1).mean() >= 0.9, (sw, ref["sweeps"])
+
+
+F32_VARIANTS = {"tensor_cores": 0, "ffma_tiles": bsvd.FLAG_F32_FFMA, "fp64_angles": bsvd.FLAG_WIDE_ANGLES,
+                "ffma_fp64_angles": bsvd.FLAG_F32_FFMA | bsvd.FLAG_WIDE_ANGLES}
+
+
+@pytest.mark.parametrize("variant", sorted(F32_VARIANTS))
+@pytest.mark.parametrize("m,n,nb", [(128, 64, 16), (100, 72, 16), (72, 100, 16), (45, 37, 8), (130, 64, 16),
+                                    (33, 19, 4)])
+def test_fp32_gram_and_update_variants(variant, m, n, nb):
+    """Real FP32 with the Gram blocks and rotation updates on the tensor cores
+    (split TF32; the default for nb = 8, 16), on the FMA register tiles, and
+    with the rotations and pair test in FP64: each meets the FP32 bounds
+    against the FP64 oracle.  Shapes with ragged 16-row tiles included."""
+    rng = np.random.default_rng(m * 31 + n + nb)
+    mats = random_mats(rng, 6, m, n, np.float32)
+    S, U, V, info, sw = run_gpu(mats, nb=nb, flags=F32_VARIANTS[variant])
+    ref = oracle.gesvj(mats)
+    assert_parity(mats, S, U, V, info, ref["S"], f"{variant} {m}x{n} nb{nb}")
+
+
+@pytest.mark.parametrize("variant", ["tensor_cores", "ffma_tiles", "fp64_angles"])
+def test_fp32_variants_tall128x64_workload(variant):
+    mats = synth.matrices("tall128x64_f32", range(24))
+    S, U, V, info, sw = run_gpu(mats, nb=16, tol=30 * 2.0 ** -24, flags=F32_VARIANTS[variant])
+    ref = oracle.gesvj(mats, tol=30 * 2.0 ** -53)
+    assert_parity(mats, S, U, V, info, ref["S"], variant)
+
+
+def test_complex64_fp64_angles():
+    rng = np.random.default_rng(77)
+    mats = random_mats(rng, 4, 60, 44, np.complex64)
+    S, U, V, info, sw = run_gpu(mats, nb=8, flags=bsvd.FLAG_WIDE_ANGLES)
+    ref = oracle.gesvj(mats)
+    assert_parity(mats, S, U, V, info, ref["S"], "c64 fp64 angles")
