@@ -303,31 +303,32 @@ def run_reference_square32(args, world):
     print(json.dumps(line), flush=True)
 
 
-# complex64 matrices with min(m, n) >= 128 run as one variable-shape
-# multi-kernel batch beside the persistent launch (flags bit 6), which stops
-# issuing sweeps once they have converged (bit 4); FP32 stays persistent
-UNEVEN_FLAGS = 64 | 16
+# matrices with min(m, n) >= 128 run as one variable-shape multi-kernel
+# batch per type beside the persistent launches (flags bit 6, and bit 10 for
+# real FP32; measured 3.53 s against 3.68 s per step with FP32 kept
+# persistent); bit 4 is the host-checked stop, used only where graphs are off
+UNEVEN_FLAGS = 64 | 16 | 1024
 SPLIT_K = 128
 
 
-def uneven_launches(groups, res, steps, nb=16):
-    """Kernel launches of one uneven step: one persistent launch per type,
-    and for the complex64 split the multi-kernel batch's load, sweeps (each
-    L_max - 1 rounds of Gram, eigensolver and update, then the convergence
-    kernel; issued in fours until all have converged) and three finalisation
-    kernels."""
-    n = len(res)
+def uneven_launches(groups, res, plans, steps, nb=16):
+    """Kernel launches of one uneven step: one persistent launch per segment
+    of each type, and for the complex64 split the multi-kernel batch's load,
+    sweeps (each L_max - 1 rounds of Gram, eigensolver and update, then the
+    convergence and loop-control kernels; the device stops the loop once all
+    have converged) and three finalisation kernels."""
+    n = sum(plans[dt][2] for dt in res)
     for dt, r in res.items():
         if not np.issubdtype(dt, np.complexfloating):
             continue
         sw = r.sweeps.cpu().numpy()
-        big = [(x.shape, k) for x, k in zip(groups[dt], sw) if min(x.shape) >= SPLIT_K]
+        big = [(x.shape, k) for x, k, w in zip(groups[dt], sw, plans[dt][1]) if w == 2]
         if not big:
             continue
         l = max(-(-min(s) // nb) for s, _ in big)
         L = l + (l & 1)
-        issued = 4 * -(-int(max(k for _, k in big)) // 4)
-        n += 1 + issued * (3 * (L - 1) + 1) + 3
+        issued = int(max(k for _, k in big))
+        n += 1 + issued * (3 * (L - 1) + 2) + 3
     return n * steps
 
 
@@ -370,7 +371,7 @@ def run_uneven(args, rank, world, local):
             s = side[dt]
             if s is not stream:
                 s.wait_event(start)
-            res[dt] = bsvd.gesvj_batched(T, path=path, stream=s, flags=UNEVEN_FLAGS)
+            res[dt] = bsvd.gesvj_batched(T, path=path, stream=s, flags=args.uneven_flags)
         for s in side.values():
             if s is not stream:
                 done = torch.cuda.Event()
@@ -378,6 +379,18 @@ def run_uneven(args, rank, world, local):
                 stream.wait_event(done)
         return res
 
+    # per-bucket autotuning (untimed set-up, like the paper's offline
+    # decision layer): block width per (type, M, N rounded to powers of two)
+    # bucket, timed on a sample of each bucket with persistent launches
+    tuning = {}
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        for dt, T in dev_mats.items():
+            tuning[np.dtype(dt).name] = bsvd.autotune_batched(T, sample=args.tune_sample)
+        tune_s = time.perf_counter() - t0
+    # how each matrix runs: its block width and where W and V live (the
+    # per-bucket decision layer), and the launches per type
+    plans = {dt: bsvd.persistent_plan(dt, [x.shape for x in groups[dt]], flags=args.uneven_flags) for dt in groups}
     for _ in range(max(1, args.warmup)):
         solve_all("persistent")
     barrier()
@@ -392,23 +405,38 @@ def run_uneven(args, rank, world, local):
     ms = max_over_ranks(a.elapsed_time(b) / args.steps, dist, dev)
     value = B * world / (ms * 1e-3)
     flops = 0.0
+    buckets = {}
     for dt, r in res.items():
         sw = r.sweeps.cpu().numpy()
-        for x, k in zip(groups[dt], sw):
+        nbs, where, _ = plans[dt]
+        for x, k, nb_, w in zip(groups[dt], sw, nbs, where):
             m, n = x.shape
-            f = matrix_flops(max(m, n), min(m, n), 16, [k])
+            f = matrix_flops(max(m, n), min(m, n), int(nb_), [k])      # at the executed block width
             flops += 4 * f if np.iscomplexobj(x) else f
+            key = f"{np.dtype(dt).name} nb={int(nb_)} {['global slot', 'shared memory', 'multi-kernel'][int(w)]}"
+            seg = buckets.setdefault(key, {"matrices": 0, "k_min": 10 ** 9, "k_max": 0})
+            seg["matrices"] += 1
+            seg["k_min"] = min(seg["k_min"], min(m, n))
+            seg["k_max"] = max(seg["k_max"], min(m, n))
     info = np.concatenate([r.info.cpu().numpy() for r in res.values()])
     line = {"metric": "batch SVD matrices/s (uneven sizes, FP32 + complex64)", "value": value,
             "unit": "matrices/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+c64", "data": "synthetic",
             "config": {"workload": "uneven: m ~ U{8..512}, n ~ U{8..m}, entries U(-1,1), half complex64",
-                       "matrices_per_rank": B,
-                       "path": "one persistent launch per type, one stream each; complex64 with k >= 128 "
-                               "as one variable-shape multi-kernel batch beside it",
+                       "matrices_per_rank": B, "flags": args.uneven_flags,
+                       "path": "persistent launches per type (one per block width x shared memory / global "
+                               "slot segment, block width per size bucket, autotuned), one stream per type; "
+                               "matrices with k >= 128 as one variable-shape multi-kernel batch per type "
+                               "beside them",
                        "l2": "inputs larger than L2"},
-            "gpu_launches": uneven_launches(groups, res, args.steps), "info_nonzero": int((info != 0).sum()),
+            "gpu_launches": uneven_launches(groups, res, plans, args.steps), "info_nonzero": int((info != 0).sum()),
+            "segments": buckets,
+            "autotune": ({"seconds": tune_s, "sample_per_bucket": args.tune_sample,
+                          "buckets": {k: [[b["M"], b["N"], b["nb"]] + [round(b["ms"][w], 3) for w in (4, 8, 16)]
+                                          for b in v] for k, v in tuning.items()},
+                          "columns": "M, N (rounded up to powers of two), chosen nb, ms at nb 4, 8, 16"}
+                         if tuning else None),
             "gflops": flops / (ms * 1e-3) / 1e9,
             "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAK_FP32 / 1e12,
                          "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAK_FP32,
@@ -557,7 +585,7 @@ def run_serving(args, rank, world, local):
     rate = args.rate or cfg["rate"]
     seconds = args.seconds or cfg["seconds"]
     pool = {}
-    srv = bsvd.Server(int(args.arena_gb * 1e9), max_inflight=32)
+    srv = bsvd.Server(int(args.arena_gb * 1e9), max_inflight=32, fp64_prec=args.fp64_prec)
     # warm-up: a short low-rate stream (first launches set kernel attributes)
     for _ in range(max(1, args.warmup)):
         serve_stream(srv, 500.0, 0.2, 30.0, 1000 + rank, pool)
@@ -587,6 +615,7 @@ def run_serving(args, rank, world, local):
                                    "30% FP64 / 20% complex64, kappa log-uniform 1e2..1e6, logrand sigma, "
                                    "Haar factors; inputs from a pool of 2 matrices per (bin, shape, type)",
                        "arena_gb": args.arena_gb, "max_inflight": 32, "jobs": "U, Sigma, V",
+                       "fp64_prec": args.fp64_prec + " (FP64 / complex128 requests above 256 columns)",
                        "results": "left in the arena and released on completion (not copied back)",
                        "l2": "inputs read once from page-locked host memory"},
             "latency_ms": main["latency_ms"], "serving": main, "rate_sweep": sweep,
@@ -952,6 +981,8 @@ def run_square(args, rank, world, local):
     sampler = ClockSampler(gpu_uuid(torch, dev))
     sampler.__enter__()
     for t, dt in (("d", torch.float64), ("s", torch.float32)):
+        if t not in args.square_dtypes:
+            continue
         for n in sizes:
             B = args.batch if args.batch != BATCH else {64: 2000, 128: 1000, 256: 200, 512: 50}.get(n, 32)
             rng = synth.rng_for(synth.SEED_BASE + 7, n * 2 + (t == "s"))
@@ -972,16 +1003,19 @@ def run_square(args, rank, world, local):
             print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
     sampler.__exit__(None, None, None)
     head = max(rows, key=lambda r: (r["dtype"] == "d", r["n"]))
-    line = {"metric": f"batch SVD matrices/s (square {head['n']}x{head['n']} FP64, U[0,1])",
+    peak_head = PEAK_FP64 if head["dtype"] == "d" else PEAK_FP32
+    line = {"metric": f"batch SVD matrices/s (square {head['n']}x{head['n']} "
+                      f"{'FP64' if head['dtype'] == 'd' else 'FP32'}, U[0,1])",
             "value": head["matrices_per_s"], "unit": "matrices/s", "n_gpus": world, "steps": args.steps,
             "warmup": 1, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if head["dtype"] == "d" else "f32", "data": "synthetic",
             "config": {"workload": "square: n x n, entries U[0,1], FP64 and FP32, U, Sigma, V; median of steps",
                        "flags": args.square_flags,
                        "l2": "L2 flushed (256 MB write) before every timed call"},
-            "roofline": {"bound": "alu", "achieved": head["tflops"], "peak": PEAK_FP64 / 1e12,
-                         "unit": "TFLOP/s", "frac": head["tflops"] * 1e12 / PEAK_FP64, "traffic": None,
-                         "kernel": f"FP64 solve at n = {head['n']} (multi-kernel path above ~100 columns)",
+            "roofline": {"bound": "alu", "achieved": head["tflops"], "peak": peak_head / 1e12,
+                         "unit": "TFLOP/s", "frac": head["tflops"] * 1e12 / peak_head, "traffic": None,
+                         "kernel": f"{head['dtype'].upper()} solve at n = {head['n']} (multi-kernel path above "
+                                   "~100 columns)",
                          "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"},
             "roofline_fp32": [{"n": r["n"], "achieved": r["tflops"], "peak": PEAK_FP32 / 1e12,
                                "frac": r["tflops"] * 1e12 / PEAK_FP32} for r in rows if r["dtype"] == "s"],
@@ -1036,14 +1070,21 @@ def main():
                          "U[0,1] batches, n = 64..512")
     ap.add_argument("--sizes", type=int, nargs="*", default=None, help="square: the sizes n")
     ap.add_argument("--square-flags", type=int, default=0, help="square: bsvd_opts.flags of every solve")
+    ap.add_argument("--square-dtypes", default="ds", help="square: types to run, of 'd' and 's'")
     ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (default 50,000)")
     ap.add_argument("--seconds", type=float, default=0.0, help="serving: stream length (default 10 s)")
     ap.add_argument("--drain", type=float, default=10.0, help="serving: seconds to drain after arrivals")
     ap.add_argument("--arena-gb", type=float, default=40.0, help="serving: device-memory budget")
+    ap.add_argument("--fp64-prec", default="mixed", choices=["native", "mixed"],
+                    help="serving: precision path of large FP64 requests (FP64 accuracy either way)")
     ap.add_argument("--sweep-rates", type=float, nargs="*", default=[25, 50, 100, 200])
     ap.add_argument("--sweep-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="mixed96: skip the optional mixed variants")
+    ap.add_argument("--uneven-flags", type=int, default=UNEVEN_FLAGS,
+                    help="uneven: bsvd_opts.flags of the persistent calls (default: split complex64 k >= 128)")
+    ap.add_argument("--no-autotune", action="store_true", help="uneven: skip the per-bucket autotuning")
+    ap.add_argument("--tune-sample", type=int, default=64, help="uneven: autotuning sample per bucket")
     ap.add_argument("--no-per-shape", action="store_true",
                     help="uneven: skip the one-launch-per-shape comparison (thousands of launches)")
     args = ap.parse_args()

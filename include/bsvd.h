@@ -71,10 +71,17 @@ typedef enum {
                                call then synchronises `stream`); FP64 comparison path   */
     BSVD_PATH_BLOCKED = 3,  /* the multi-kernel path with Designs 2-4 (one inner sweep,
                                fused update, masks); any matrix size; asynchronous      */
-    BSVD_PATH_PERSISTENT = 4 /* pointer-array form: all shapes in one persistent launch;
-                               CTAs take matrices from a work queue, largest first, each
-                               solved whole with W and V in a per-CTA workspace slot
-                               (the strided form treats it as AUTO)                      */
+    BSVD_PATH_PERSISTENT = 4 /* pointer-array form: all shapes in a few persistent
+                               launches, one per segment (block width x where W and V
+                               live); each matrix takes the block width of its shape
+                               (opts->nb, else the bucket's autotuned choice, else the
+                               AUTO rule) and keeps W and V in shared memory when they
+                               fit in half an SM (at least two CTAs per SM), else in a per-CTA
+                               global workspace slot; CTAs take matrices from their
+                               segment's queue, largest first, each solved whole.  The
+                               segments run on streams the handle owns, forked from and
+                               joined back to `stream` (the strided form treats it as
+                               AUTO)                                                     */
 } bsvd_path;
 
 typedef enum {
@@ -127,8 +134,13 @@ typedef struct {
                           instead of the tensor cores (split-TF32 mma, FP32 accuracy);
                           bit 8: single-precision data (and the FP32 sweeps of MIXED)
                           take the pair test and the rotation (Eq. sin-cos) in FP64,
-                          rounded once to FP32                                         */
-    int prec;          /* bsvd_prec; MIXED only for d/z and the strided form                 */
+                          rounded once to FP32;
+                          bit 9: BSVD_PATH_PERSISTENT keeps every matrix in a global
+                          workspace slot (no shared-memory segments);
+                          bit 10: with bit 6, real FP32 batches split the same way      */
+    int prec;          /* bsvd_prec; MIXED only for d/z.  Pointer-array batches run MIXED per
+                          shape group (also with BSVD_PATH_PERSISTENT), reading A and
+                          writing S, U, V through the pointer arrays                     */
     int reserved[5];
 } bsvd_opts;
 
@@ -152,6 +164,24 @@ int bsvd_version(void);
 bsvd_status bsvd_gesvj_workspace(bsvd_handle handle, char dtype, int batch, const int* m_arr,
                                  const int* n_arr, int uniform, bsvd_job jobu, bsvd_job jobv,
                                  const bsvd_opts* opts, size_t* bytes);
+
+/*
+ * How a BSVD_PATH_PERSISTENT pointer-array call with these arguments would
+ * run each matrix (host only; nothing is launched).  The per-(shape, type)
+ * decision layer of Sec. 4.2 ("Computation of the Gram Matrices") made
+ * explicit for batches of mixed shapes.  Arguments:
+ *   1 handle  2 dtype ('s','d','c','z')  3 batch >= 0  4 m[batch]  5 n[batch]
+ *   6 jobu  7 jobv  8 opts  9 nb_out[batch]  10 where_out[batch]  11 launches
+ * nb_out[i] receives matrix i's block width; where_out[i] 1 for W and V in
+ * shared memory, 0 for a global workspace slot, 2 for the variable-shape
+ * multi-kernel batch (flags bit 6), -1 for an empty matrix; *launches (may
+ * be NULL) the number of persistent launches.  All arrays are host memory,
+ * owned by the caller.  Returns BSVD_ERR_INVALID (bsvd_last_arg) for a bad
+ * argument and BSVD_ERR_NOT_IMPLEMENTED for an unsupported block width.
+ */
+bsvd_status bsvd_persistent_plan(bsvd_handle handle, char dtype, int batch, const int* m_arr, const int* n_arr,
+                                 bsvd_job jobu, bsvd_job jobv, const bsvd_opts* opts, int* nb_out,
+                                 int* where_out, int* launches);
 
 /*
  * Strided batch: every matrix has the same m and n; matrix i of X starts at
@@ -229,6 +259,38 @@ bsvd_status bsvd_autotune(bsvd_handle handle, char dtype, bsvd_job jobu, bsvd_jo
                           int n, const void* dA, int lda, long long strideA, void* d_work,
                           size_t work_bytes, const bsvd_opts* base, bsvd_opts* best, float* times_ms,
                           void* stream);
+
+/*
+ * Autotuner for pointer-array batches of mixed shapes (the decision layer of
+ * Sec. 4.2, per size bucket).  The batch's matrices are grouped into buckets
+ * (type, m and n rounded up to powers of two, jobu, jobv); for each bucket
+ * persistent launches (BSVD_PATH_PERSISTENT) of a sample -- its first
+ * min(count, sample) matrices, fewer (at least 2) for shapes whose M N^2
+ * exceeds 64 times that of a 64 x 64 matrix -- are timed with block width
+ * nb = 4 (N <= 32), 8 and 16 (N >= 16), N rounded up to a power of two
+ * (the width also fixes the threads per matrix: 64, 128, 256 per CTA; on
+ * chip or in global slots follows from the fit at each width).  The fastest width
+ * whose every matrix converged is recorded in the handle for the bucket;
+ * later persistent calls (and AUTO strided calls) of that bucket use it.  The
+ * caller's matrices are read only; the sample's results go to d_work.
+ * Synchronises `stream`.  Workspace: bsvd_autotune_batched_workspace bytes.
+ * Arguments:
+ *   1 handle 2 dtype 3 jobu 4 jobv 5 batch 6 m[] 7 n[] (host) 8 dA[] (device
+ *   array of device pointers) 9 lda[] (host) 10 d_work 11 work_bytes 12 base
+ *   (NULL = defaults) 13 sample >= 1 14 max_out >= 0 15 bucket_mn[2 max_out]
+ *   16 nb_out[max_out] 17 times_ms[3 max_out] 18 buckets 19 stream
+ * For the first max_out buckets (in ascending key order), bucket_mn receives
+ * the bucket's rounded (M, N), nb_out the chosen width (0: no candidate
+ * converged), times_ms the three candidates' times (-1: not run); each may
+ * be NULL.  *buckets (may be NULL) receives the number of buckets.
+ */
+bsvd_status bsvd_autotune_batched_workspace(bsvd_handle handle, char dtype, int batch, const int* m, const int* n,
+                                            bsvd_job jobu, bsvd_job jobv, const bsvd_opts* base, int sample,
+                                            size_t* bytes);
+bsvd_status bsvd_autotune_batched(bsvd_handle handle, char dtype, bsvd_job jobu, bsvd_job jobv, int batch,
+                                  const int* m, const int* n, const void* const* dA, const int* lda, void* d_work,
+                                  size_t work_bytes, const bsvd_opts* base, int sample, int max_out,
+                                  int* bucket_mn, int* nb_out, float* times_ms, int* buckets, void* stream);
 
 /*
  * Strided FP64 batch that allocates nothing (the paper has no counterpart).
@@ -321,8 +383,11 @@ typedef struct {
                            multi-kernel batches hold at most max_inflight - max(2, max_inflight/4) */
     int max_batch;      /* requests per persistent batch; 0 = 4096                               */
     int big_k;          /* min(m, n) above which the multi-kernel path serves; 0 = 256          */
-    int max_big_batch;  /* requests per multi-kernel batch; 0 = 64                               */
-    int reserved[4];    /* zero                                                                  */
+    int max_big_batch;  /* requests per multi-kernel batch; 0 = 8                                */
+    int fp64_prec;      /* bsvd_prec of FP64 / complex128 requests on the multi-kernel path
+                           (min(m, n) > big_k): BSVD_PREC_NATIVE (0, default) or
+                           BSVD_PREC_MIXED (FP32 sweeps + FP64 polish, FP64 accuracy)      */
+    int reserved[3];    /* zero                                                                  */
 } bsvd_server_opts;
 
 double bsvd_server_clock(void);

@@ -26,7 +26,7 @@ PATHS = {"auto": 0, "fused": 1, "plain": 2, "blocked": 3, "persistent": 4}
 PATH_NAMES = {v: k for k, v in PATHS.items()}
 FLAG_NO_V_CORRECTION, FLAG_TWO_STAGE, FLAG_NO_MASKS, FLAG_NO_GRAPH, FLAG_SYNC_CHECK, FLAG_QR = 1, 2, 4, 8, 16, 32
 FLAG_SPLIT_LARGE = 64
-FLAG_F32_FFMA, FLAG_WIDE_ANGLES = 128, 256
+FLAG_F32_FFMA, FLAG_WIDE_ANGLES, FLAG_NO_ONCHIP, FLAG_SPLIT_F32 = 128, 256, 512, 1024
 DTYPES = {torch.float32: "s", torch.float64: "d", torch.complex64: "c", torch.complex128: "z"}
 REAL = {torch.float32: torch.float32, torch.float64: torch.float64,
         torch.complex64: torch.float32, torch.complex128: torch.float64}
@@ -38,7 +38,8 @@ EXPORTS = (
     "bsvd_version", "bsvd_gesvj_workspace",
     "bsvd_sgesvj_strided", "bsvd_dgesvj_strided", "bsvd_cgesvj_strided", "bsvd_zgesvj_strided",
     "bsvd_sgesvj_batched", "bsvd_dgesvj_batched", "bsvd_cgesvj_batched", "bsvd_zgesvj_batched",
-    "bsvd_dgesvj_strided_noalloc", "bsvd_autotune_workspace", "bsvd_autotune",
+    "bsvd_dgesvj_strided_noalloc", "bsvd_autotune_workspace", "bsvd_autotune", "bsvd_persistent_plan",
+    "bsvd_autotune_batched_workspace", "bsvd_autotune_batched",
     "bsvd_gesvj_host_workspace", "bsvd_sgesvj_strided_host", "bsvd_dgesvj_strided_host",
     "bsvd_cgesvj_strided_host", "bsvd_zgesvj_strided_host",
     "bsvd_server_clock", "bsvd_server_create", "bsvd_server_submit", "bsvd_server_replay",
@@ -59,7 +60,7 @@ class BsvdError(RuntimeError):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("max_inflight", ctypes.c_int), ("max_batch", ctypes.c_int), ("big_k", ctypes.c_int),
-                ("max_big_batch", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("max_big_batch", ctypes.c_int), ("fp64_prec", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class Opts(ctypes.Structure):
@@ -110,6 +111,12 @@ def load() -> ctypes.CDLL:
                     ctypes.POINTER(Opts), P]
             L.bsvd_autotune.argtypes = [P, ctypes.c_char, I, I, I, I, I, P, I, LL, P, SZ,
                                         ctypes.POINTER(Opts), ctypes.POINTER(Opts), P, P]
+            L.bsvd_persistent_plan.argtypes = [P, ctypes.c_char, I, P, P, I, I, ctypes.POINTER(Opts), P, P,
+                                               ctypes.POINTER(I)]
+            L.bsvd_autotune_batched_workspace.argtypes = [P, ctypes.c_char, I, P, P, I, I, ctypes.POINTER(Opts),
+                                                          I, ctypes.POINTER(SZ)]
+            L.bsvd_autotune_batched.argtypes = [P, ctypes.c_char, I, I, I, P, P, P, P, P, SZ,
+                                                ctypes.POINTER(Opts), I, I, P, P, P, ctypes.POINTER(I), P]
             D = ctypes.c_double
             L.bsvd_server_clock.restype = D
             L.bsvd_server_create.argtypes = [P, SZ, ctypes.POINTER(ServerOpts), ctypes.POINTER(P)]
@@ -342,7 +349,7 @@ def _flat_outputs(sizes, dtype, device):
 
 def gesvj_batched(mats, compute_u: bool = True, compute_v: bool = True, *, nb: int = 0,
                   tol: float = 0.0, max_sweeps: int = 0, inner_sweeps: int = 0, path="auto",
-                  flags: int = 0, stream=None):
+                  flags: int = 0, prec="native", stream=None):
     """SVD of a list of CUDA matrices of any shapes (one dtype) through the
     pointer-array entry point.  Returns lists S, U, V and info, sweeps.
 
@@ -376,7 +383,7 @@ def gesvj_batched(mats, compute_u: bool = True, compute_v: bool = True, *, nb: i
         Vf, offV, pV = _flat_outputs(n_np * k_np, dt, dev)
     info = torch.empty(B, dtype=torch.int32, device=dev)
     sweeps = torch.empty(B, dtype=torch.int32, device=dev)
-    o = make_opts(nb, tol, max_sweeps, inner_sweeps, path, flags)
+    o = make_opts(nb, tol, max_sweeps, inner_sweeps, path, flags, prec)
     L, h = load(), handle()
     t = DTYPES[dt]
     nbytes = ctypes.c_size_t()
@@ -406,6 +413,80 @@ def gesvj_batched(mats, compute_u: bool = True, compute_v: bool = True, *, nb: i
     V = [Vf.narrow(0, int(o_), int(n * k)).view(int(k), int(n)).t() for o_, n, k in zip(offV, n_np, k_np)] \
         if compute_v else None
     return SVDResult(S, U, V, info, sweeps)
+
+
+_NP_CHAR = {np.dtype(np.float32): "s", np.dtype(np.float64): "d", np.dtype(np.complex64): "c",
+            np.dtype(np.complex128): "z"}
+
+
+def type_char(dtype) -> str:
+    """'s', 'd', 'c' or 'z' for a torch dtype, a numpy dtype or the character itself."""
+    if isinstance(dtype, str):
+        return dtype
+    if dtype in DTYPES:
+        return DTYPES[dtype]
+    return _NP_CHAR[np.dtype(dtype)]
+
+
+def persistent_plan(dtype, shapes, compute_u: bool = True, compute_v: bool = True, **opts):
+    """How a path="persistent" batch of these (m, n) shapes would run each
+    matrix: returns (nb, where, launches) with nb and where per matrix (where:
+    1 shared memory, 0 global slot, 2 the variable-shape multi-kernel batch,
+    -1 empty).  Host only (``bsvd_persistent_plan``)."""
+    B = len(shapes)
+    ms = (ctypes.c_int * max(B, 1))(*[int(s[0]) for s in shapes])
+    ns = (ctypes.c_int * max(B, 1))(*[int(s[1]) for s in shapes])
+    nb = (ctypes.c_int * max(B, 1))()
+    where = (ctypes.c_int * max(B, 1))()
+    launches = ctypes.c_int(0)
+    opts.setdefault("path", "persistent")
+    o = make_opts(**opts)
+    t = type_char(dtype)
+    L, h = load(), handle()
+    _check(L.bsvd_persistent_plan(h, t.encode(), B, ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(ns, ctypes.c_void_p),
+                                  int(compute_u), int(compute_v), ctypes.byref(o), ctypes.cast(nb, ctypes.c_void_p),
+                                  ctypes.cast(where, ctypes.c_void_p), ctypes.byref(launches)),
+           "bsvd_persistent_plan")
+    return np.array(nb[:B], dtype=np.int32), np.array(where[:B], dtype=np.int32), int(launches.value)
+
+
+def autotune_batched(mats, compute_u: bool = True, compute_v: bool = True, *, sample: int = 64, stream=None,
+                     **opts):
+    """Per-bucket autotuning of a list of CUDA matrices of mixed shapes (one
+    dtype) for path="persistent" (``bsvd_autotune_batched``): times block
+    widths 4, 8, 16 on a sample of each (type, M, N rounded to powers of two,
+    jobs) bucket and records the winners in the library handle.  Returns a
+    list of {"M", "N", "nb", "ms": {nb: ms}} per bucket."""
+    mats = [column_major(x) for x in mats]
+    dt = mats[0].dtype
+    dev = mats[0].device
+    B = len(mats)
+    ms = (ctypes.c_int * max(B, 1))(*[int(x.shape[0]) for x in mats])
+    ns = (ctypes.c_int * max(B, 1))(*[int(x.shape[1]) for x in mats])
+    lda = (ctypes.c_int * max(B, 1))(*[leading_dim(x) for x in mats])
+    pA = torch.tensor([x.data_ptr() for x in mats], dtype=torch.int64, device=dev)
+    o = make_opts(**opts)
+    L, h = load(), handle()
+    t = DTYPES[dt]
+    nbytes = ctypes.c_size_t()
+    _check(L.bsvd_autotune_batched_workspace(h, t.encode(), B, ctypes.cast(ms, ctypes.c_void_p),
+                                             ctypes.cast(ns, ctypes.c_void_p), int(compute_u), int(compute_v),
+                                             ctypes.byref(o), int(sample), ctypes.byref(nbytes)),
+           "bsvd_autotune_batched_workspace")
+    work = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=dev)
+    cap = 4096
+    mn = (ctypes.c_int * (2 * cap))()
+    nb = (ctypes.c_int * cap)()
+    tm = (ctypes.c_float * (3 * cap))()
+    nbk = ctypes.c_int(0)
+    _check(L.bsvd_autotune_batched(h, t.encode(), int(compute_u), int(compute_v), B, ctypes.cast(ms, ctypes.c_void_p),
+                                   ctypes.cast(ns, ctypes.c_void_p), pA.data_ptr(), ctypes.cast(lda, ctypes.c_void_p),
+                                   work.data_ptr(), work.numel(), ctypes.byref(o), int(sample), cap,
+                                   ctypes.cast(mn, ctypes.c_void_p), ctypes.cast(nb, ctypes.c_void_p),
+                                   ctypes.cast(tm, ctypes.c_void_p), ctypes.byref(nbk), _stream_ptr(stream)),
+           "bsvd_autotune_batched")
+    return [{"M": mn[2 * i], "N": mn[2 * i + 1], "nb": nb[i],
+             "ms": {w: tm[3 * i + c] for c, w in enumerate((4, 8, 16))}} for i in range(min(nbk.value, cap))]
 
 
 def autotune(A: torch.Tensor, compute_u: bool = True, compute_v: bool = True, *, stream=None, **opts):
@@ -453,7 +534,7 @@ class Server:
     """
 
     def __init__(self, arena_bytes: int, *, max_inflight: int = 0, max_batch: int = 0, big_k: int = 0,
-                 max_big_batch: int = 0, device=None):
+                 max_big_batch: int = 0, fp64_prec="native", device=None):
         self.lib = load()
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.device = dev
@@ -461,6 +542,7 @@ class Server:
         o = ServerOpts()
         o.max_inflight, o.max_batch, o.big_k = int(max_inflight), int(max_batch), int(big_k)
         o.max_big_batch = int(max_big_batch)
+        o.fp64_prec = PRECS[fp64_prec] if isinstance(fp64_prec, str) else int(fp64_prec)
         srv = ctypes.c_void_p()
         with torch.cuda.device(dev):
             st = self.lib.bsvd_server_create(self.arena.data_ptr(), self.arena.numel(), ctypes.byref(o),

@@ -36,6 +36,7 @@ struct BlockedArgs {
     void* U; long long sU; int ldu; void* const* Up; const int* ldup;
     void* V; long long sV; int ldv; void* const* Vp; const int* ldvp;
     const int* index;
+    int in_local;              // 1: strided A and V0 by launch position, outputs by matrix id
     int* info; int* sweeps;
     double tol;
     int max_sweeps, inner_sweeps, flags;

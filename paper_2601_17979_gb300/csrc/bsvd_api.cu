@@ -42,6 +42,10 @@ struct bsvd_handle_s {
     cudaStream_t split = nullptr;                          // split uneven batches: the multi-kernel part
     cudaEvent_t split_ev[2] = {nullptr, nullptr};          // fork from, join to the caller's stream
     int split_device = -1;
+    cudaStream_t pstream[5] = {};                          // persistent segments beyond the first
+    cudaEvent_t pevent[5] = {};                            // their joins
+    cudaEvent_t pfork = nullptr;                           // the fork from the caller's stream
+    int pstream_device = -1, pstream_prio = 0;
 };
 
 namespace {
@@ -105,7 +109,7 @@ bool resolve(const bsvd_opts* o, bool single, int N, Resolved& r) {
     std::memset(&z, 0, sizeof z);
     if (!o) o = &z;
     if (o->nb < 0 || o->max_sweeps < 0 || o->inner_sweeps < 0 || o->tol < 0 || o->path < 0 ||
-        o->path > BSVD_PATH_PERSISTENT || o->flags < 0 || o->flags > 511 || o->prec < 0 ||
+        o->path > BSVD_PATH_PERSISTENT || o->flags < 0 || o->flags > 2047 || o->prec < 0 ||
         o->prec > BSVD_PREC_MIXED || (o->prec == BSVD_PREC_MIXED && single))
         return false;
     r.nb = o->nb ? o->nb : (N >= 48 ? 16 : (N >= 12 ? 8 : 4));
@@ -145,8 +149,9 @@ typedef cudaError_t (*launch_fn)(int, const FusedArgs&, int, size_t, cudaStream_
 typedef cudaError_t (*blocked_fn)(int, const BlockedArgs&, void*, cudaStream_t, bool, bool, cudaStream_t);
 typedef cudaError_t (*blocked_var_fn)(int, const BlockedArgs&, const bsvd::BlkVarPlan&, void*, cudaStream_t,
                                       cudaStream_t);
-typedef cudaError_t (*persist_fn)(int, const bsvd::PersistArgs&, int, int, cudaStream_t);
+typedef cudaError_t (*persist_fn)(int, bool, size_t, const bsvd::PersistArgs&, int, int, cudaStream_t);
 typedef long long (*slot_fn)(int, int, int);
+typedef size_t (*psmem_fn)(int, size_t, int);
 
 struct TypeOps {
     bool single;
@@ -157,18 +162,23 @@ struct TypeOps {
     persist_fn persist;
     slot_fn slot;
     blocked_var_fn blocked_var;
+    psmem_fn smem;
 };
 
 TypeOps ops_for(char t) {
     switch (t) {
         case 's': return {true, 4, bsvd::fused_plan_s, bsvd::fused_launch_s, bsvd::blocked_run_s,
-                          bsvd::persist_launch_s, bsvd::persist_slot_s, bsvd::blocked_run_var_s};
+                          bsvd::persist_launch_s, bsvd::persist_slot_s, bsvd::blocked_run_var_s,
+                          bsvd::persist_smem_s};
         case 'd': return {false, 8, bsvd::fused_plan_d, bsvd::fused_launch_d, bsvd::blocked_run_d,
-                          bsvd::persist_launch_d, bsvd::persist_slot_d, bsvd::blocked_run_var_d};
+                          bsvd::persist_launch_d, bsvd::persist_slot_d, bsvd::blocked_run_var_d,
+                          bsvd::persist_smem_d};
         case 'c': return {true, 8, bsvd::fused_plan_c, bsvd::fused_launch_c, bsvd::blocked_run_c,
-                          bsvd::persist_launch_c, bsvd::persist_slot_c, bsvd::blocked_run_var_c};
+                          bsvd::persist_launch_c, bsvd::persist_slot_c, bsvd::blocked_run_var_c,
+                          bsvd::persist_smem_c};
         default:  return {false, 16, bsvd::fused_plan_z, bsvd::fused_launch_z, bsvd::blocked_run_z,
-                          bsvd::persist_launch_z, bsvd::persist_slot_z, bsvd::blocked_run_var_z};
+                          bsvd::persist_launch_z, bsvd::persist_slot_z, bsvd::blocked_run_var_z,
+                          bsvd::persist_smem_z};
     }
 }
 
@@ -180,6 +190,7 @@ struct Plan {
     int threads = 0;
     int nb = 0;
     bool two_stage = false, masks = true, host_sync = false;
+    bool mixed = false;        // FP64 output by the mixed-precision path (bytes: its workspace)
     size_t bytes = 0;          // workspace of the multi-kernel path
 };
 
@@ -287,11 +298,21 @@ bsvd_status plan_mixed(int max_smem, char t, int m, int n, int batch, bool wantU
     return BSVD_OK;
 }
 
+// Pointer-array inputs and outputs of one shape group of a pointer-array
+// batch (device arrays indexed by matrix id; `index` lists the group's ids).
+struct PtrIO {
+    const void* const* Ap; const int* ldap;
+    void* const* Sp;
+    void* const* Up; const int* ldup;
+    void* const* Vp; const int* ldvp;
+    const int* index;
+};
+
 bsvd_status mixed_impl(char t, bsvd_handle h, bool wantU, bool wantV, int batch, int m, int n,
                        const void* dA, int lda, long long sA, void* dS, long long sS, void* dU,
                        int ldu, long long sU, void* dV, int ldv, long long sV, int* d_info,
                        int* d_sweeps, void* d_work, size_t work_bytes, const Resolved& r,
-                       cudaStream_t s) {
+                       cudaStream_t s, const PtrIO* io = nullptr) {
     MixedPlan mp;
     bsvd_status st = plan_mixed(h->max_smem, t, m, n, batch, wantU, wantV, r, mp);
     if (st != BSVD_OK) return st;
@@ -302,6 +323,7 @@ bsvd_status mixed_impl(char t, bsvd_handle h, bool wantU, bool wantV, int batch,
     bsvd::MixedArgs ma;
     ma.m = m; ma.n = n; ma.M = M; ma.N = N; ma.trans = trans;
     ma.A = dA; ma.sA = sA; ma.lda = lda;
+    ma.Ap = io ? io->Ap : nullptr; ma.ldap = io ? io->ldap : nullptr; ma.index = io ? io->index : nullptr;
     ma.A32 = w + mp.off[0]; ma.V32 = w + mp.off[1];
     ma.V64 = w + mp.off[4]; ma.Vtmp = w + mp.off[5]; ma.E = w + mp.off[6]; ma.Ahat = w + mp.off[7];
     void* S32 = w + mp.off[2];
@@ -337,6 +359,17 @@ bsvd_status mixed_impl(char t, bsvd_handle h, bool wantU, bool wantV, int batch,
     const int pldu = trans ? ldv : ldu, pldv = trans ? ldu : ldv;
     const long long psU = trans ? sV : sU, psV = trans ? sU : sV;
     const bool pu = trans ? wantV : wantU, pv = trans ? wantU : wantV;
+    // pointer-array outputs: by matrix id, the strided A_hat and V64 by
+    // position in the group (in_local)
+    auto outputs = [&](auto& a) {
+        if (!io) return;
+        a.S = nullptr; a.U = nullptr; a.V = nullptr;
+        a.Sp = io->Sp;
+        a.Up = trans ? io->Vp : io->Up; a.ldup = trans ? io->ldvp : io->ldup;
+        a.Vp = trans ? io->Up : io->Vp; a.ldvp = trans ? io->ldup : io->ldvp;
+        a.index = io->index;
+        a.in_local = 1;
+    };
     if (mp.p64.blocked) {
         BlockedArgs a = blocked_args(M, N, batch, pu, pv, mp.r64, mp.p64.masks);
         a.A = ma.Ahat; a.sA = (long long)M * N; a.lda = M;
@@ -345,6 +378,7 @@ bsvd_status mixed_impl(char t, bsvd_handle h, bool wantU, bool wantV, int batch,
         a.U = pU; a.sU = psU; a.ldu = pldu;
         a.V = pV; a.sV = psV; a.ldv = pldv;
         a.info = d_info; a.sweeps = d_sweeps;
+        outputs(a);
         e = o64.blocked(mp.p64.nb, a, w + mp.off64, s, mp.p64.two_stage, mp.p64.host_sync, capture_stream(h, r.flags));
     } else {
         FusedArgs& a = mp.p64.a;
@@ -354,6 +388,7 @@ bsvd_status mixed_impl(char t, bsvd_handle h, bool wantU, bool wantV, int batch,
         a.U = pU; a.sU = psU; a.ldu = pldu;
         a.V = pV; a.sV = psV; a.ldv = pldv;
         a.info = d_info; a.sweeps = d_sweeps;
+        outputs(a);
         e = o64.launch(mp.p64.nb, a, batch, mp.p64.smem, s);
     }
     return e == cudaSuccess ? BSVD_OK : fail_cuda(h, e);
@@ -543,7 +578,14 @@ bsvd_status plan_batched(bsvd_handle h, char t, int max_smem, const TypeOps& ops
         const int mm = kv.first.first, nn = kv.first.second;
         if (!resolve(opts, ops.single, std::min(mm, nn), res[gi])) return BSVD_ERR_INVALID;
         apply_tuned(h, t, mm, nn, wantU, wantV, opts, res[gi]);
-        if (std::min(mm, nn) > 0) {
+        if (std::min(mm, nn) > 0 && res[gi].prec == BSVD_PREC_MIXED) {
+            MixedPlan mp;
+            bsvd_status st = plan_mixed(max_smem, t, mm, nn, (int)kv.second.size(), wantU, wantV, res[gi], mp);
+            if (st != BSVD_OK) return st;
+            plans[gi].mixed = true;
+            plans[gi].bytes = mp.bytes;
+            total += align256(mp.bytes);
+        } else if (std::min(mm, nn) > 0) {
             bsvd_status st = plan_group(max_smem, ops, mm, nn, (int)kv.second.size(), wantU, wantV,
                                         res[gi], plans[gi]);
             if (st != BSVD_OK) return st;
@@ -554,11 +596,35 @@ bsvd_status plan_batched(bsvd_handle h, char t, int max_smem, const TypeOps& ops
     return BSVD_OK;
 }
 
-// ---- one persistent launch for a pointer-array batch of any shapes -----------
+// ---- persistent launches for a pointer-array batch of any shapes -------------
+// The batch is cut into segments, one per (block width, where the working
+// arrays live): each matrix gets the block width of its own shape -- the
+// caller's nb, else the autotuned choice recorded in the handle for its
+// bucket (type, M and N rounded up to powers of two, jobs), else the AUTO
+// rule from min(m, n) -- and runs with W and V in shared memory when they
+// fit there at the kernel's occupancy (the on-chip kernel's layout), else in
+// a global-memory slot of its CTA.  Each segment is one persistent launch
+// whose CTAs take its matrices largest first; the segments run on streams
+// forked from the caller's (the largest segment on the caller's own), so a
+// later segment's CTAs fill the SMs that an earlier one's tail leaves idle.
+constexpr int kMaxPersistSegs = 6;
+constexpr int kFlagNoOnChip = 512;   // flags bit 9: every matrix in a global slot
+
+struct PersistSeg {
+    int nb = 0;
+    bool onchip = false;
+    std::vector<int> ids;          // largest first
+    int grid = 0, maxN = 0;
+    long long slot = 0;            // elements per global slot
+    size_t wv = 0;                 // bytes of W + V of the segment's largest matrix on chip
+    size_t ws_off = 0;             // byte offset of the segment's slots in the workspace
+    double work = 0;               // sum of M N^2
+};
+
 struct PersistPlan {
-    int nb = 0, grid = 0, maxN = 0, count = 0;
-    long long slot = 0;
-    std::vector<int> order;     // non-empty ids, largest first
+    std::vector<PersistSeg> segs;
+    std::vector<int> nb_of, where_of;   // per matrix: block width; 0 slot, 1 on chip, -1 not here
+    int count = 0, maxN = 0;
     size_t ints = 0, bytes = 0;
 };
 
@@ -572,50 +638,131 @@ int device_sms_or_default(bsvd_handle h) {
     return 152;   // GB300
 }
 
-bsvd_status plan_persistent(int sms, const TypeOps& ops, int batch, const int* m, const int* n,
-                            const bsvd_opts* opts, PersistPlan& pp, const std::vector<char>* excl = nullptr) {
-    pp.maxN = 0;
-    pp.order.clear();
+// Block width of one matrix of a persistent batch.
+int persist_nb(bsvd_handle h, char t, int m, int n, bool wantU, bool wantV, const bsvd_opts* opts) {
+    if (opts && opts->nb) return opts->nb;
+    if (h) {
+        auto it = h->tuned.find(tune_key(t, m, n, wantU, wantV));
+        if (it != h->tuned.end() && fused_nb(it->second.nb)) return it->second.nb;
+    }
+    const int k = std::min(m, n);
+    return k >= 48 ? 16 : (k >= 12 ? 8 : 4);
+}
+
+// Shared memory one CTA of an on-chip launch may take: half the SM's 228 KB
+// less the 1 KB the hardware reserves per CTA, so that at least two CTAs
+// share an SM -- a CTA that filled the SM would hold it alone for its whole
+// matrix, and no other launch's CTA could start there meanwhile.
+size_t onchip_budget(const TypeOps& ops, int max_smem) {
+    (void)ops;
+    return std::min((size_t)(228 * 1024 / 2 - 1024), (size_t)max_smem);
+}
+
+bsvd_status plan_persistent(bsvd_handle h, char t, int sms, int max_smem, const TypeOps& ops, int batch,
+                            const int* m, const int* n, bool wantU, bool wantV, const bsvd_opts* opts,
+                            PersistPlan& pp, const std::vector<char>* excl = nullptr) {
+    pp = PersistPlan();
+    pp.nb_of.assign(batch, 0);
+    pp.where_of.assign(batch, -1);
+    std::vector<int> ids;
     for (int i = 0; i < batch; ++i) {
         if (excl && (*excl)[i]) continue;             // solved on the multi-kernel path
         const int k = std::min(m[i], n[i]);
-        if (k > 0) pp.order.push_back(i);
+        if (k > 0) ids.push_back(i);
         pp.maxN = std::max(pp.maxN, k);
     }
     // largest first: cost ~ M N^2 per sweep
-    std::stable_sort(pp.order.begin(), pp.order.end(), [&](int a, int b) {
-        const double ca = (double)std::max(m[a], n[a]) * std::min(m[a], n[a]) * std::min(m[a], n[a]);
-        const double cb = (double)std::max(m[b], n[b]) * std::min(m[b], n[b]) * std::min(m[b], n[b]);
-        return ca > cb;
-    });
-    pp.count = (int)pp.order.size();
-    const int nbo = opts ? opts->nb : 0;
-    pp.nb = nbo ? nbo : (pp.maxN >= 48 ? 16 : (pp.maxN >= 12 ? 8 : 4));
-    if (!fused_nb(pp.nb)) return BSVD_ERR_NOT_IMPLEMENTED;
-    pp.slot = 0;
-    for (int id : pp.order) pp.slot = std::max(pp.slot, ops.slot(pp.nb, m[id], n[id]));
-    // resident CTAs per SM of the persistent kernel: two (register cap 128)
-    // except for complex128
-    pp.grid = std::max(1, std::min(pp.count, sms * (ops.elt == 16 ? 1 : 2)));
-    pp.ints = align256((size_t)(6 * (size_t)batch + 1) * sizeof(int));
-    pp.bytes = pp.ints + align256((size_t)pp.grid * pp.slot * ops.elt);
+    auto cost = [&](int i) { return (double)std::max(m[i], n[i]) * std::min(m[i], n[i]) * std::min(m[i], n[i]); };
+    std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    pp.count = (int)ids.size();
+    const bool allow_onchip = !(opts && (opts->flags & kFlagNoOnChip));
+    const size_t budget = onchip_budget(ops, max_smem);
+    std::map<std::pair<int, int>, int> seg_of;         // (nb, on chip) -> segment
+    for (int id : ids) {
+        const int nb = persist_nb(h, t, m[id], n[id], wantU, wantV, opts);
+        if (!fused_nb(nb)) return BSVD_ERR_NOT_IMPLEMENTED;
+        const size_t wv = ops.slot(nb, m[id], n[id]) * ops.elt;
+        const bool onchip = allow_onchip && ops.smem(nb, wv, pp.maxN) <= budget;
+        auto key = std::make_pair(nb, onchip ? 1 : 0);
+        auto it = seg_of.find(key);
+        if (it == seg_of.end()) {
+            it = seg_of.emplace(key, (int)pp.segs.size()).first;
+            pp.segs.emplace_back();
+            pp.segs.back().nb = nb;
+            pp.segs.back().onchip = onchip;
+        }
+        PersistSeg& sg = pp.segs[it->second];
+        sg.ids.push_back(id);
+        sg.maxN = std::max(sg.maxN, std::min(m[id], n[id]));
+        if (onchip) sg.wv = std::max(sg.wv, wv);
+        else sg.slot = std::max(sg.slot, ops.slot(nb, m[id], n[id]));
+        sg.work += cost(id);
+        pp.nb_of[id] = nb;
+        pp.where_of[id] = onchip ? 1 : 0;
+    }
+    std::stable_sort(pp.segs.begin(), pp.segs.end(),
+                     [](const PersistSeg& a, const PersistSeg& b) { return a.work > b.work; });
+    if ((int)pp.segs.size() > kMaxPersistSegs) return BSVD_ERR_NOT_IMPLEMENTED;
+    // ints: lda, ldu, ldv, m, n (batch each), the segments' queues (count in
+    // all), one queue head per segment
+    pp.ints = align256(((size_t)5 * batch + pp.count + kMaxPersistSegs) * sizeof(int));
+    size_t pos = pp.ints;
+    for (PersistSeg& sg : pp.segs) {
+        // global slots: two resident CTAs per SM (register cap 128) except
+        // for complex128, and that many slots; on chip the launch sizes the
+        // grid by the kernel's occupancy, capped here by the matrix count
+        const int per_sm = (ops.elt == 16 ? 1 : 2) * (16 / sg.nb);   // 256 threads' worth of CTAs, x2
+        sg.grid = sg.onchip ? std::max(1, (int)sg.ids.size())
+                            : std::max(1, std::min((int)sg.ids.size(), sms * per_sm));
+        sg.ws_off = pos;
+        if (!sg.onchip) pos += align256((size_t)sg.grid * sg.slot * ops.elt);
+    }
+    pp.bytes = pos;
     return BSVD_OK;
 }
 
-bsvd_status persistent_impl(bsvd_handle h, const TypeOps& ops, bool wantU, bool wantV, int batch,
+// The side streams of the persistent segments, with the priority of the
+// caller's stream `s` (the server runs small requests on high-priority
+// streams): made once per device and priority.
+cudaError_t persist_streams(bsvd_handle h, cudaStream_t s) {
+    int prio = 0;
+    cudaError_t e = cudaStreamGetPriority(s, &prio);
+    if (e != cudaSuccess) return e;
+    if (h->pstream[0] && h->pstream_device == h->device && h->pstream_prio == prio) return cudaSuccess;
+    for (int i = 0; i < kMaxPersistSegs - 1; ++i) {
+        if (h->pstream[i]) cudaStreamDestroy(h->pstream[i]);
+        if (h->pevent[i]) cudaEventDestroy(h->pevent[i]);
+        h->pstream[i] = nullptr;
+        h->pevent[i] = nullptr;
+    }
+    if (h->pfork) cudaEventDestroy(h->pfork);
+    h->pfork = nullptr;
+    e = cudaEventCreateWithFlags(&h->pfork, cudaEventDisableTiming);
+    for (int i = 0; i < kMaxPersistSegs - 1 && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithPriority(&h->pstream[i], cudaStreamNonBlocking, prio);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->pevent[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) {
+        h->pstream_device = h->device;
+        h->pstream_prio = prio;
+    }
+    return e;
+}
+
+bsvd_status persistent_impl(bsvd_handle h, char t, const TypeOps& ops, bool wantU, bool wantV, int batch,
                             const int* m, const int* n, const void* const* dA, const int* lda,
                             void* const* dS, void* const* dU, const int* ldu, void* const* dV,
                             const int* ldv, int* d_info, int* d_sweeps, void* d_work,
                             size_t work_bytes, const bsvd_opts* opts, cudaStream_t s, int* d_done = nullptr,
                             const int* d_abort = nullptr, const std::vector<char>* excl = nullptr) {
     PersistPlan pp;
-    bsvd_status st = plan_persistent(h->sm_count, ops, batch, m, n, opts, pp, excl);
+    bsvd_status st = plan_persistent(h, t, h->sm_count, h->max_smem, ops, batch, m, n, wantU, wantV, opts, pp, excl);
     if (st != BSVD_OK) return st;
     if (!d_work || work_bytes < pp.bytes) return BSVD_ERR_WORKSPACE;
     Resolved r;
     if (!resolve(opts, ops.single, pp.maxN, r)) return fail_arg(h, 18);
-    // ints: lda, ldu, ldv, m, n, order (batch each), then the queue head
-    std::vector<int> host((size_t)6 * batch + 1, 0);
+    // ints: lda, ldu, ldv, m, n (batch each), the queues, the heads (zero)
+    std::vector<int> host((size_t)5 * batch + pp.count + kMaxPersistSegs, 0);
     for (int i = 0; i < batch; ++i) {
         host[i] = lda[i];
         host[batch + i] = wantU ? ldu[i] : 1;
@@ -623,7 +770,13 @@ bsvd_status persistent_impl(bsvd_handle h, const TypeOps& ops, bool wantU, bool 
         host[3 * (size_t)batch + i] = m[i];
         host[4 * (size_t)batch + i] = n[i];
     }
-    std::copy(pp.order.begin(), pp.order.end(), host.begin() + 5 * (size_t)batch);
+    std::vector<size_t> qpos;
+    size_t q = 5 * (size_t)batch;
+    for (const PersistSeg& sg : pp.segs) {
+        qpos.push_back(q);
+        std::copy(sg.ids.begin(), sg.ids.end(), host.begin() + q);
+        q += sg.ids.size();
+    }
     int* dws = static_cast<int*>(d_work);
     cudaError_t e = cudaMemcpyAsync(dws, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail_cuda(h, e);
@@ -634,27 +787,53 @@ bsvd_status persistent_impl(bsvd_handle h, const TypeOps& ops, bool wantU, bool 
             if (e != cudaSuccess) return fail_cuda(h, e);
         }
     if (pp.count == 0) return BSVD_OK;
-    bsvd::PersistArgs p;
-    std::memset(&p, 0, sizeof p);
-    FusedArgs& a = p.base;
-    a.Ap = dA; a.ldap = dws;
-    a.Sp = dS;
-    a.Up = dU; a.ldup = dws + batch;
-    a.Vp = dV; a.ldvp = dws + 2 * batch;
-    a.info = d_info; a.sweeps = d_sweeps;
-    a.wantU = wantU; a.wantV = wantV;
-    a.tol = r.tol; a.max_sweeps = r.max_sweeps; a.inner_sweeps = r.inner_sweeps; a.flags = r.flags;
-    p.mm = dws + 3 * batch;
-    p.nn = dws + 4 * batch;
-    p.order = dws + 5 * batch;
-    p.count = pp.count;
-    p.head = dws + 6 * batch;
-    p.ws = static_cast<char*>(d_work) + pp.ints;
-    p.slot_elems = pp.slot;
-    p.done = d_done;
-    p.abort = d_abort;
-    e = ops.persist(pp.nb, p, pp.grid, pp.maxN, s);
-    return e == cudaSuccess ? BSVD_OK : fail_cuda(h, e);
+    const int nseg = (int)pp.segs.size();
+    if (nseg > 1) {
+        if ((e = persist_streams(h, s)) != cudaSuccess) return fail_cuda(h, e);
+        if ((e = cudaEventRecord(h->pfork, s)) != cudaSuccess) return fail_cuda(h, e);
+    }
+    cudaError_t first_err = cudaSuccess;
+    for (int k = 0; k < nseg; ++k) {
+        const PersistSeg& sg = pp.segs[k];
+        cudaStream_t ss = k == 0 ? s : h->pstream[k - 1];
+        if (k > 0 && (e = cudaStreamWaitEvent(ss, h->pfork, 0)) != cudaSuccess) {
+            first_err = e;
+            break;
+        }
+        bsvd::PersistArgs p;
+        std::memset(&p, 0, sizeof p);
+        FusedArgs& a = p.base;
+        a.Ap = dA; a.ldap = dws;
+        a.Sp = dS;
+        a.Up = dU; a.ldup = dws + batch;
+        a.Vp = dV; a.ldvp = dws + 2 * batch;
+        a.info = d_info; a.sweeps = d_sweeps;
+        a.wantU = wantU; a.wantV = wantV;
+        a.tol = r.tol; a.max_sweeps = r.max_sweeps; a.inner_sweeps = r.inner_sweeps; a.flags = r.flags;
+        p.mm = dws + 3 * batch;
+        p.nn = dws + 4 * batch;
+        p.order = dws + qpos[k];
+        p.count = (int)sg.ids.size();
+        p.head = dws + 5 * batch + pp.count + k;
+        p.ws = static_cast<char*>(d_work) + sg.ws_off;
+        p.slot_elems = sg.slot;
+        p.done = d_done;
+        p.abort = d_abort;
+        e = ops.persist(sg.nb, sg.onchip, sg.wv, p, sg.grid, sg.maxN, ss);
+        if (e != cudaSuccess) {
+            first_err = e;
+            break;
+        }
+    }
+    // join every side stream that was forked, also after a failure: the
+    // caller's stream owns the results
+    if (nseg > 1)
+        for (int k = 1; k < nseg; ++k) {
+            cudaError_t ej = cudaEventRecord(h->pevent[k - 1], h->pstream[k - 1]);
+            if (ej == cudaSuccess) ej = cudaStreamWaitEvent(s, h->pevent[k - 1], 0);
+            if (first_err == cudaSuccess) first_err = ej;
+        }
+    return first_err == cudaSuccess ? BSVD_OK : fail_cuda(h, first_err);
 }
 
 // ---- flags bit 6: split an uneven complex64 persistent batch ------------------
@@ -668,10 +847,13 @@ bsvd_status persistent_impl(bsvd_handle h, const TypeOps& ops, bool wantU, bool 
 // it the empty sweeps up to max_sweeps cost 0.3 s).  For FP32 the
 // variable-shape batch was slower (1.31 s against 1.20 s), so the flag
 // leaves other types in the persistent launch.
-constexpr int kFlagSplit = 64, kSplitK = 128;
+// Flags bit 10 extends the split to real FP32 (measured on the uneven
+// workload; the default leaves FP32 in the persistent launches).
+constexpr int kFlagSplit = 64, kFlagSplitF32 = 1024, kSplitK = 128;
 
 bool split_large(const TypeOps& ops, const bsvd_opts* opts) {
-    return ops.single && ops.elt == 8 && opts && opts->path == BSVD_PATH_PERSISTENT && (opts->flags & kFlagSplit);
+    if (!ops.single || !opts || opts->path != BSVD_PATH_PERSISTENT || !(opts->flags & kFlagSplit)) return false;
+    return ops.elt == 8 || (opts->flags & kFlagSplitF32);
 }
 
 struct SplitPlan {
@@ -714,14 +896,15 @@ cudaError_t split_streams(bsvd_handle h) {
     return e;
 }
 
-bsvd_status split_impl(bsvd_handle h, const TypeOps& ops, bool wantU, bool wantV, int batch, const int* m,
+bsvd_status split_impl(bsvd_handle h, char t, const TypeOps& ops, bool wantU, bool wantV, int batch, const int* m,
                        const int* n, const void* const* dA, const int* lda, void* const* dS, void* const* dU,
                        const int* ldu, void* const* dV, const int* ldv, int* d_info, int* d_sweeps,
                        void* d_work, size_t work_bytes, const bsvd_opts* opts, cudaStream_t s) {
     SplitPlan sp;
     plan_split(ops, batch, m, n, opts, sp);
     PersistPlan pp;
-    bsvd_status st = plan_persistent(h->sm_count, ops, batch, m, n, opts, pp, &sp.excl);
+    bsvd_status st = plan_persistent(h, t, h->sm_count, h->max_smem, ops, batch, m, n, wantU, wantV, opts, pp,
+                                     &sp.excl);
     if (st != BSVD_OK) return st;
     if (!d_work || work_bytes < pp.bytes + sp.bytes) return BSVD_ERR_WORKSPACE;
     const int count = (int)sp.ids.size();
@@ -735,7 +918,7 @@ bsvd_status split_impl(bsvd_handle h, const TypeOps& ops, bool wantU, bool wantV
     }
     // the persistent launch first: with flags bit 4 the multi-kernel part
     // below returns only once its matrices have converged
-    st = persistent_impl(h, ops, wantU, wantV, batch, m, n, dA, lda, dS, dU, ldu, dV, ldv, d_info, d_sweeps,
+    st = persistent_impl(h, t, ops, wantU, wantV, batch, m, n, dA, lda, dS, dU, ldu, dV, ldv, d_info, d_sweeps,
                          d_work, pp.bytes, opts, s, nullptr, nullptr, &sp.excl);
     if (st != BSVD_OK || count == 0) return st;
     cudaStream_t side = h->split;
@@ -797,15 +980,25 @@ bsvd_status batched_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
     }
     if (d_work && (reinterpret_cast<uintptr_t>(d_work) & 15) != 0) return fail_arg(h, 16);
     const TypeOps ops = ops_for(t);
-    if (opts && opts->prec == BSVD_PREC_MIXED) return BSVD_ERR_NOT_IMPLEMENTED;   // strided form only
     if (opts && (opts->flags & kFlagQR)) return BSVD_ERR_NOT_IMPLEMENTED;      // strided form only
+    // MIXED runs per shape group (with PERSISTENT too): the mixed-precision
+    // path of the strided form on each group, inputs and outputs through the
+    // pointer arrays
+    const bool mixed = opts && opts->prec == BSVD_PREC_MIXED;
+    bsvd_opts om;
+    if (mixed && opts->path == BSVD_PATH_PERSISTENT) {
+        om = *opts;
+        om.path = BSVD_PATH_AUTO;
+        om.flags &= ~(kFlagSplit | kFlagSplitF32 | kFlagNoOnChip);
+        opts = &om;
+    }
     if (opts && opts->path == BSVD_PATH_PERSISTENT) {
         bsvd_status st = refresh_device(h);
         if (st != BSVD_OK) return st;
         if (split_large(ops, opts))
-            return split_impl(h, ops, wantU, wantV, batch, m, n, dA, lda, dS, dU, ldu, dV, ldv, d_info,
+            return split_impl(h, t, ops, wantU, wantV, batch, m, n, dA, lda, dS, dU, ldu, dV, ldv, d_info,
                               d_sweeps, d_work, work_bytes, opts, static_cast<cudaStream_t>(stream));
-        return persistent_impl(h, ops, wantU, wantV, batch, m, n, dA, lda, dS, dU, ldu, dV, ldv, d_info,
+        return persistent_impl(h, t, ops, wantU, wantV, batch, m, n, dA, lda, dS, dU, ldu, dV, ldv, d_info,
                                d_sweeps, d_work, work_bytes, opts, static_cast<cudaStream_t>(stream));
     }
     Groups groups;
@@ -856,6 +1049,15 @@ bsvd_status batched_impl(char t, bsvd_handle h, bsvd_job jobu, bsvd_job jobv, in
             }
             continue;
         }
+        if (p.mixed) {
+            const PtrIO io{reinterpret_cast<const void* const*>(dA), dws, dS, dU, dws + batch, dV, dws + 2 * batch,
+                           index};
+            bsvd_status sm = mixed_impl(t, h, wantU, wantV, count, mm, nn, nullptr, 1, 0, nullptr, 0, nullptr, 1, 0,
+                                        nullptr, 1, 0, d_info, d_sweeps, region, p.bytes, r, s, &io);
+            if (sm != BSVD_OK) return sm;
+            region += align256(p.bytes);
+            continue;
+        }
         if (p.blocked) {
             BlockedArgs a = blocked_args(mm, nn, count, wantU, wantV, r, p.masks);
             a.Ap = dA; a.ldap = dws;
@@ -897,7 +1099,7 @@ bsvd_status bsvd::persistent_with_flags(bsvd_handle h, char t, bool wantU, bool 
     if (!h || batch < 1) return BSVD_ERR_INVALID;
     bsvd_status st = refresh_device(h);
     if (st != BSVD_OK) return st;
-    return persistent_impl(h, ops_for(t), wantU, wantV, batch, m, n, dA, lda, dS, dU, ldu, dV, ldv, d_info,
+    return persistent_impl(h, t, ops_for(t), wantU, wantV, batch, m, n, dA, lda, dS, dU, ldu, dV, ldv, d_info,
                            d_sweeps, d_work, work_bytes, opts, s, d_done, d_abort);
 }
 
@@ -972,6 +1174,11 @@ bsvd_status bsvd_destroy(bsvd_handle handle) {
         if (handle->split) cudaStreamDestroy(handle->split);
         for (cudaEvent_t ev : handle->split_ev)
             if (ev) cudaEventDestroy(ev);
+        for (cudaStream_t s : handle->pstream)
+            if (s) cudaStreamDestroy(s);
+        for (cudaEvent_t ev : handle->pevent)
+            if (ev) cudaEventDestroy(ev);
+        if (handle->pfork) cudaEventDestroy(handle->pfork);
     }
     delete handle;
     return BSVD_OK;
@@ -1043,15 +1250,21 @@ bsvd_status bsvd_gesvj_workspace(bsvd_handle handle, char dtype, int batch, cons
         if (n_arr[i] < 0) return fail_arg(handle, 5);
         groups[{m_arr[i], n_arr[i]}].push_back(i);
     }
-    if (opts && opts->prec == BSVD_PREC_MIXED) return BSVD_ERR_NOT_IMPLEMENTED;   // strided form only
     if (opts && (opts->flags & kFlagQR)) return BSVD_ERR_NOT_IMPLEMENTED;      // strided form only
+    bsvd_opts om;
+    if (opts && opts->prec == BSVD_PREC_MIXED && opts->path == BSVD_PATH_PERSISTENT) {   // per shape group
+        om = *opts;
+        om.path = BSVD_PATH_AUTO;
+        om.flags &= ~(kFlagSplit | kFlagSplitF32 | kFlagNoOnChip);
+        opts = &om;
+    }
     if (opts && opts->path == BSVD_PATH_PERSISTENT) {
         SplitPlan sp;
         const bool split = split_large(ops, opts);
         if (split) plan_split(ops, batch, m_arr, n_arr, opts, sp);
         PersistPlan pp;
-        bsvd_status st = plan_persistent(device_sms_or_default(handle), ops, batch, m_arr, n_arr, opts, pp,
-                                         split ? &sp.excl : nullptr);
+        bsvd_status st = plan_persistent(handle, dtype, device_sms_or_default(handle), max_smem, ops, batch, m_arr,
+                                         n_arr, wantU, wantV, opts, pp, split ? &sp.excl : nullptr);
         if (st == BSVD_OK) *bytes = pp.bytes + (split ? sp.bytes : 0);
         return st;
     }
@@ -1061,6 +1274,40 @@ bsvd_status bsvd_gesvj_workspace(bsvd_handle handle, char dtype, int batch, cons
                                   res, *bytes);
     if (st == BSVD_ERR_INVALID) return fail_arg(handle, 9);
     return st;
+}
+
+bsvd_status bsvd_persistent_plan(bsvd_handle handle, char dtype, int batch, const int* m_arr, const int* n_arr,
+                                 bsvd_job jobu, bsvd_job jobv, const bsvd_opts* opts, int* nb_out, int* where_out,
+                                 int* launches) {
+    if (!handle) return BSVD_ERR_INVALID;
+    handle->last_arg = 0;
+    if (dtype != 's' && dtype != 'd' && dtype != 'c' && dtype != 'z') return fail_arg(handle, 2);
+    if (batch < 0) return fail_arg(handle, 3);
+    if (batch > 0 && (!m_arr || !n_arr)) return fail_arg(handle, !m_arr ? 4 : 5);
+    if (batch > 0 && (!nb_out || !where_out)) return fail_arg(handle, !nb_out ? 9 : 10);
+    for (int i = 0; i < batch; ++i) {
+        if (m_arr[i] < 0) return fail_arg(handle, 4);
+        if (n_arr[i] < 0) return fail_arg(handle, 5);
+    }
+    const TypeOps ops = ops_for(dtype);
+    const bool wantU = jobu == BSVD_JOB_SOME, wantV = jobv == BSVD_JOB_SOME;
+    SplitPlan sp;
+    const bool split = split_large(ops, opts);
+    if (split) plan_split(ops, batch, m_arr, n_arr, opts, sp);
+    PersistPlan pp;
+    bsvd_status st = plan_persistent(handle, dtype, device_sms_or_default(handle), device_smem_or_default(handle),
+                                     ops, batch, m_arr, n_arr, wantU, wantV, opts, pp, split ? &sp.excl : nullptr);
+    if (st != BSVD_OK) return st;
+    for (int i = 0; i < batch; ++i) {
+        nb_out[i] = pp.nb_of[i];
+        where_out[i] = pp.where_of[i];
+        if (split && sp.excl[i]) {
+            nb_out[i] = sp.nb;
+            where_out[i] = 2;
+        }
+    }
+    if (launches) *launches = (int)pp.segs.size();
+    return BSVD_OK;
 }
 
 bsvd_status bsvd_autotune_workspace(bsvd_handle handle, char dtype, int batch, int m, int n,
@@ -1153,6 +1400,230 @@ bsvd_status bsvd_autotune(bsvd_handle handle, char dtype, bsvd_job jobu, bsvd_jo
     tune_cand(best_c, o.path, o.nb);
     *best = o;
     handle->tuned[tune_key(dtype, m, n, wantU, wantV)] = bsvd_tuned{o.path, o.nb, best_ms};
+    return BSVD_OK;
+}
+
+
+namespace {
+
+// ---- autotuner for pointer-array batches of mixed shapes ---------------------
+// Per bucket (type, M and N rounded up to powers of two, jobs) of the batch,
+// persistent launches of a sample of the bucket's matrices are timed with
+// each block width (4, 8, 16; the block width also fixes the threads per
+// matrix: 64, 128 or 256 per CTA); on chip or in global slots follows from
+// the fit at each width.  The winner is recorded in the handle and later
+// persistent calls (and AUTO strided calls) of the bucket follow it.
+constexpr int kTuneNbs[3] = {4, 8, 16};
+
+struct BatchTuneBucket {
+    bsvd_tune_key key;
+    std::vector<int> ids;          // the sample (first matrices of the bucket)
+};
+
+struct BatchTuneLayout {
+    std::vector<BatchTuneBucket> buckets;
+    size_t bytes = 0;              // the largest sample's need
+};
+
+// Sample outputs (S, U, V per matrix, 256-byte aligned), pointer arrays,
+// info and sweeps, then the persistent workspace of the candidate.
+struct SampleLayout {
+    std::vector<size_t> oS, oU, oV;
+    size_t ptr_off = 0, info_off = 0, work_off = 0, bytes = 0;
+};
+
+size_t sample_layout(const TypeOps& ops, const std::vector<int>& ids, const int* m, const int* n, bool wantU,
+                     bool wantV, SampleLayout& L) {
+    const size_t rsz = ops.single ? 4 : 8;
+    const size_t B = ids.size();
+    size_t pos = 0;
+    L.oS.resize(B); L.oU.resize(B); L.oV.resize(B);
+    for (size_t i = 0; i < B; ++i) {
+        const int mm = m[ids[i]], nn = n[ids[i]], k = std::min(mm, nn);
+        L.oS[i] = pos; pos += align256((size_t)k * rsz);
+        L.oU[i] = pos; if (wantU) pos += align256((size_t)mm * k * ops.elt);
+        L.oV[i] = pos; if (wantV) pos += align256((size_t)nn * k * ops.elt);
+    }
+    L.ptr_off = pos; pos += 4 * align256(B * sizeof(void*));
+    L.info_off = pos; pos += align256(2 * B * sizeof(int));
+    L.work_off = pos;
+    return pos;
+}
+
+bsvd_opts tune_opts(const bsvd_opts* base, int nb) {
+    bsvd_opts o;
+    if (base) o = *base;
+    else std::memset(&o, 0, sizeof o);
+    o.path = BSVD_PATH_PERSISTENT;
+    o.nb = nb;
+    o.prec = BSVD_PREC_NATIVE;
+    o.flags &= (1 | 128 | 256 | 512);   // numerics and on-chip choice; no split, QR or host checks
+    return o;
+}
+
+void batch_tune_layout(bsvd_handle h, char t, int batch, const int* m, const int* n, bool wantU, bool wantV,
+                       const bsvd_opts* base, int sample, BatchTuneLayout& BL) {
+    const TypeOps ops = ops_for(t);
+    std::map<bsvd_tune_key, std::vector<int>> by;
+    for (int i = 0; i < batch; ++i)
+        if (std::min(m[i], n[i]) > 0) by[tune_key(t, m[i], n[i], wantU, wantV)].push_back(i);
+    BL = BatchTuneLayout();
+    for (auto& kv : by) {
+        BatchTuneBucket b;
+        b.key = kv.first;
+        // the sample: at most `sample` matrices, and for large shapes no more
+        // than about 64 matrices of 64 x 64 worth of work (M N^2), at least 2
+        const int M = std::get<1>(kv.first), N = std::get<2>(kv.first);
+        const double per = (double)M * N * N, budget = 64.0 * 64 * 64 * 64;
+        const size_t cap = (size_t)std::max(2.0, std::min((double)sample, budget / per));
+        b.ids.assign(kv.second.begin(), kv.second.begin() + std::min(kv.second.size(), cap));
+        SampleLayout L;
+        const size_t fixed = sample_layout(ops, b.ids, m, n, wantU, wantV, L);
+        std::vector<int> sm, sn;
+        for (int id : b.ids) { sm.push_back(m[id]); sn.push_back(n[id]); }
+        for (int nb : kTuneNbs) {
+            const bsvd_opts o = tune_opts(base, nb);
+            PersistPlan pp;
+            if (plan_persistent(h, t, device_sms_or_default(h), device_smem_or_default(h), ops, (int)b.ids.size(),
+                                sm.data(), sn.data(), wantU, wantV, &o, pp) == BSVD_OK)
+                BL.bytes = std::max(BL.bytes, fixed + pp.bytes);
+        }
+        BL.buckets.push_back(std::move(b));
+    }
+}
+
+}  // namespace
+
+bsvd_status bsvd_autotune_batched_workspace(bsvd_handle handle, char dtype, int batch, const int* m, const int* n,
+                                            bsvd_job jobu, bsvd_job jobv, const bsvd_opts* base, int sample,
+                                            size_t* bytes) {
+    if (!handle) return BSVD_ERR_INVALID;
+    handle->last_arg = 0;
+    if (dtype != 's' && dtype != 'd' && dtype != 'c' && dtype != 'z') return fail_arg(handle, 2);
+    if (batch < 0) return fail_arg(handle, 3);
+    if (batch > 0 && (!m || !n)) return fail_arg(handle, !m ? 4 : 5);
+    if (sample < 1) return fail_arg(handle, 9);
+    if (!bytes) return fail_arg(handle, 10);
+    for (int i = 0; i < batch; ++i)
+        if (m[i] < 0 || n[i] < 0) return fail_arg(handle, m[i] < 0 ? 4 : 5);
+    BatchTuneLayout BL;
+    batch_tune_layout(handle, dtype, batch, m, n, jobu == BSVD_JOB_SOME, jobv == BSVD_JOB_SOME, base, sample, BL);
+    *bytes = BL.bytes;
+    return BSVD_OK;
+}
+
+bsvd_status bsvd_autotune_batched(bsvd_handle handle, char dtype, bsvd_job jobu, bsvd_job jobv, int batch,
+                                  const int* m, const int* n, const void* const* dA, const int* lda, void* d_work,
+                                  size_t work_bytes, const bsvd_opts* base, int sample, int max_out,
+                                  int* bucket_mn, int* nb_out, float* times_ms, int* buckets, void* stream) {
+    if (!handle) return BSVD_ERR_INVALID;
+    handle->last_arg = 0;
+    if (dtype != 's' && dtype != 'd' && dtype != 'c' && dtype != 'z') return fail_arg(handle, 2);
+    if (jobu != BSVD_JOB_NONE && jobu != BSVD_JOB_SOME) return fail_arg(handle, 3);
+    if (jobv != BSVD_JOB_NONE && jobv != BSVD_JOB_SOME) return fail_arg(handle, 4);
+    if (batch < 0) return fail_arg(handle, 5);
+    if (batch > 0 && (!m || !n || !dA || !lda)) return fail_arg(handle, !m ? 6 : !n ? 7 : !dA ? 8 : 9);
+    if (sample < 1) return fail_arg(handle, 13);
+    if (max_out < 0) return fail_arg(handle, 14);
+    for (int i = 0; i < batch; ++i) {
+        if (m[i] < 0) return fail_arg(handle, 6);
+        if (n[i] < 0) return fail_arg(handle, 7);
+        if (lda[i] < std::max(1, m[i])) return fail_arg(handle, 9);
+    }
+    const bool wantU = jobu == BSVD_JOB_SOME, wantV = jobv == BSVD_JOB_SOME;
+    bsvd_status st = refresh_device(handle);
+    if (st != BSVD_OK) return st;
+    BatchTuneLayout BL;
+    batch_tune_layout(handle, dtype, batch, m, n, wantU, wantV, base, sample, BL);
+    if (buckets) *buckets = (int)BL.buckets.size();
+    if (batch == 0 || BL.buckets.empty()) return BSVD_OK;
+    if (!d_work || work_bytes < BL.bytes) return BSVD_ERR_WORKSPACE;
+    const TypeOps ops = ops_for(dtype);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the caller's matrix pointers, to pick each sample's
+    std::vector<const void*> hA(batch);
+    cudaError_t e = cudaMemcpyAsync(hA.data(), dA, batch * sizeof(void*), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(handle, e);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return fail_cuda(handle, cudaGetLastError());
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail_cuda(handle, cudaGetLastError()); }
+    char* w = static_cast<char*>(d_work);
+    for (size_t bi = 0; bi < BL.buckets.size(); ++bi) {
+        const BatchTuneBucket& b = BL.buckets[bi];
+        const bool out = (int)bi < max_out;
+        if (out && bucket_mn) {
+            bucket_mn[2 * bi] = std::get<1>(b.key);
+            bucket_mn[2 * bi + 1] = std::get<2>(b.key);
+        }
+        if (out && nb_out) nb_out[bi] = 0;
+        const int B = (int)b.ids.size();
+        SampleLayout L;
+        sample_layout(ops, b.ids, m, n, wantU, wantV, L);
+        std::vector<const void*> pA(B);
+        std::vector<void*> pS(B), pU(B), pV(B);
+        std::vector<int> sm(B), sn(B), ints(3 * (size_t)B);   // lda, ldu, ldv (host; copied by the call)
+        for (int i = 0; i < B; ++i) {
+            const int id = b.ids[i];
+            sm[i] = m[id]; sn[i] = n[id];
+            pA[i] = hA[id];
+            pS[i] = w + L.oS[i]; pU[i] = w + L.oU[i]; pV[i] = w + L.oV[i];
+            ints[i] = lda[id]; ints[B + i] = std::max(1, m[id]); ints[2 * B + i] = std::max(1, n[id]);
+        }
+        const size_t pa = align256((size_t)B * sizeof(void*));
+        void** dpA = reinterpret_cast<void**>(w + L.ptr_off);
+        void** dpS = reinterpret_cast<void**>(w + L.ptr_off + pa);
+        void** dpU = reinterpret_cast<void**>(w + L.ptr_off + 2 * pa);
+        void** dpV = reinterpret_cast<void**>(w + L.ptr_off + 3 * pa);
+        int* dinfo = reinterpret_cast<int*>(w + L.info_off);
+        e = cudaMemcpyAsync(dpA, pA.data(), B * sizeof(void*), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dpS, pS.data(), B * sizeof(void*), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dpU, pU.data(), B * sizeof(void*), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dpV, pV.data(), B * sizeof(void*), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host vectors go out of scope below
+        if (e != cudaSuccess) break;
+        int best_nb = 0;
+        float best_ms = 0.f;
+        const int kb = std::get<2>(b.key);                    // N rounded up to a power of two
+        for (int c = 0; c < 3; ++c) {
+            const int nb = kTuneNbs[c];
+            if (out && times_ms) times_ms[3 * bi + c] = -1.f;
+            // candidates near the shape: nb = 4 only up to 32 columns, nb = 16
+            // from 16 columns on (others pad or serialise far too much)
+            if ((nb == 4 && kb > 32) || (nb == 16 && kb < 16)) continue;
+            const bsvd_opts o = tune_opts(base, nb);
+            float ms = 0.f;
+            bool ok = true;
+            for (int rep = 0; rep < 2 && ok; ++rep) {       // the first run warms up, the second is timed
+                cudaEventRecord(e0, s);
+                st = persistent_impl(handle, dtype, ops, wantU, wantV, B, sm.data(), sn.data(),
+                                     reinterpret_cast<const void* const*>(dpA), ints.data(), dpS, dpU,
+                                     ints.data() + B, dpV, ints.data() + 2 * B, dinfo, dinfo + B,
+                                     w + L.work_off, work_bytes - L.work_off, &o, s);
+                cudaEventRecord(e1, s);
+                if (st != BSVD_OK || cudaEventSynchronize(e1) != cudaSuccess) { ok = false; break; }
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (!ok) { cudaGetLastError(); continue; }
+            std::vector<int> info(B);
+            if (cudaMemcpy(info.data(), dinfo, sizeof(int) * B, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            bool conv = true;                                    // every matrix must converge
+            for (int v : info) conv = conv && v == 0;
+            if (!conv) continue;
+            if (out && times_ms) times_ms[3 * bi + c] = ms;
+            if (best_nb == 0 || ms < best_ms) { best_nb = nb; best_ms = ms; }
+        }
+        if (best_nb) {
+            handle->tuned[b.key] = bsvd_tuned{BSVD_PATH_AUTO, best_nb, best_ms};
+            if (out && nb_out) nb_out[bi] = best_nb;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail_cuda(handle, e);
     return BSVD_OK;
 }
 

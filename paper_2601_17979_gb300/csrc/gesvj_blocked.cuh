@@ -197,7 +197,8 @@ __global__ void __launch_bounds__(kBlkThreads) blk_load(const BlockedArgs a) {
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int mid = blk_mid(a, b);
     const BlkShape sh = blk_shape(a, b);
-    const T* A = a.Ap ? static_cast<const T*>(a.Ap[mid]) : static_cast<const T*>(a.A) + (long long)mid * a.sA;
+    const int sid = a.in_local ? b : mid;                     // position of strided inputs
+    const T* A = a.Ap ? static_cast<const T*>(a.Ap[mid]) : static_cast<const T*>(a.A) + (long long)sid * a.sA;
     const int lda = a.ldap ? a.ldap[mid] : a.lda;
     R mx = 0;
     int nonfin = 0;
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(kBlkThreads) blk_load(const BlockedArgs a) {
         else          W[i + (long long)j * M] = x;
     }
     for (int e = tid; e < M * (sh.Np - N); e += NT) W[(e % M) + (long long)(N + e / M) * M] = make_s<T>(0);
-    const T* V0 = a.V0 ? static_cast<const T*>(a.V0) + (long long)mid * a.sV0 : nullptr;
+    const T* V0 = a.V0 ? static_cast<const T*>(a.V0) + (long long)sid * a.sV0 : nullptr;
     for (int e = tid; e < N * sh.Np; e += NT) {
         const int i = e % N, j = e / N;
         V[i + (long long)j * N] = (V0 && j < N) ? V0[i + (long long)j * a.ldv0] : make_s<T>(i == j && !V0 ? 1 : 0);

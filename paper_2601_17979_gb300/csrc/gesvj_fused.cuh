@@ -43,6 +43,7 @@ struct FusedArgs {
     void* U; long long sU; int ldu; void* const* Up; const int* ldup;
     void* V; long long sV; int ldv; void* const* Vp; const int* ldvp;
     const int* index;      // matrix ids of this launch, or nullptr for 0..grid-1
+    int in_local;          // 1: strided A and V0 by launch position, outputs by matrix id
     int* info; int* sweeps;
     double tol;
     int max_sweeps, inner_sweeps, flags;
@@ -142,8 +143,8 @@ constexpr int fused_min_blocks() { return std::is_same<T, float>::value ? 2 : 1;
 // blocks, rotation tables and flags are always in shared memory at the
 // offsets of `a`.  All threads of the CTA call it and return together.
 template <class T, int NB, int NG, int GT, bool OnChip>
-__device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T* const W, T* const Vs,
-                                            unsigned char* const smem) {
+__device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, const int lid, T* const W,
+                                            T* const Vs, unsigned char* const smem) {
     using R = Real<T>;
     constexpr int TWO = 2 * NB, LDG = TWO + 1, NT = NG * GT, NW = NT / 32;
 
@@ -170,7 +171,8 @@ __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T
     int* rank = reinterpret_cast<int*>(sig + ((N + 3) & ~3));  // [N]
 
     // ---- load W = A (or A^H) and find max |a| and non-finite entries ----------
-    const T* A = a.Ap ? static_cast<const T*>(a.Ap[mid]) : static_cast<const T*>(a.A) + (long long)mid * a.sA;
+    const int sid = a.in_local ? lid : mid;                    // position of strided inputs
+    const T* A = a.Ap ? static_cast<const T*>(a.Ap[mid]) : static_cast<const T*>(a.A) + (long long)sid * a.sA;
     const int lda = a.ldap ? a.ldap[mid] : a.lda;
     for (int e = tid; e < kMaxSweeps; e += NT) swflag[e] = 0;
     R mx = 0;
@@ -188,7 +190,7 @@ __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T
     if (needVs && ldvs > N)
         for (int e = tid; e < (ldvs - N) * a.Np; e += NT) Vs[N + e % (ldvs - N) + (e / (ldvs - N)) * ldvs] = make_s<T>(0);
     if (needVs) {
-        const T* V0 = a.V0 ? static_cast<const T*>(a.V0) + (long long)mid * a.sV0 : nullptr;
+        const T* V0 = a.V0 ? static_cast<const T*>(a.V0) + (long long)sid * a.sV0 : nullptr;
         for (int e = tid; e < N * a.Np; e += NT) {
             const int i = e % N, j = e / N;
             Vs[i + j * ldvs] = (V0 && j < N) ? V0[i + (long long)j * a.ldv0] : make_s<T>(i == j && !V0 ? 1 : 0);
@@ -510,23 +512,32 @@ __device__ __forceinline__ void fused_solve(const FusedArgs& a, const int mid, T
     }
 }
 
+// Resident CTAs the register allocation must allow: the type's count for
+// 256-thread CTAs, scaled up for smaller CTAs (nb = 4, 8: 64 and 128
+// threads) so that small matrices keep as many threads per SM.
+template <int Base, int NT>
+constexpr int min_blocks_for() { return Base * (256 / NT > 1 ? 256 / NT : 1); }
+
 template <class T, int NB, int NG, int GT>
-__global__ void __launch_bounds__(NG * GT, fused_min_blocks<T>())
+__global__ void __launch_bounds__(NG * GT, (min_blocks_for<fused_min_blocks<T>(), NG * GT>()))
 gesvj_fused_kernel(const FusedArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int mid = a.index ? a.index[blockIdx.x] : (int)blockIdx.x;
-    fused_solve<T, NB, NG, GT, true>(a, mid, reinterpret_cast<T*>(smem + a.offW), reinterpret_cast<T*>(smem + a.offV),
-                               smem);
+    fused_solve<T, NB, NG, GT, true>(a, mid, (int)blockIdx.x, reinterpret_cast<T*>(smem + a.offW),
+                                     reinterpret_cast<T*>(smem + a.offV), smem);
 }
 
-// Pointer-array batches of any shapes in one persistent launch: each CTA
+// Pointer-array batches of any shapes in persistent launches: each CTA
 // takes the next matrix from a work queue (ids in `order`, largest first),
-// lays it out in its own global-memory slot and solves it with the same
-// per-matrix code as the on-chip kernel.  With `done` given, the CTA raises
-// done[id] once matrix id's outputs are written, so a host that polls the
-// flags can hand each result out before the launch ends; with `abort` given,
-// a CTA that finds it set takes no further matrix (those not started keep
-// their done flag at zero).
+// lays it out in its working arrays and solves it with the same per-matrix
+// code as the on-chip kernel.  A launch serves one segment of a batch: one
+// block width, and either working arrays in shared memory (OnChip: W and V
+// of the segment's largest matrix fit there; the layout of the on-chip
+// kernel) or in the CTA's own global-memory slot.  With `done` given, the
+// CTA raises done[id] once matrix id's outputs are written, so a host that
+// polls the flags can hand each result out before the launch ends; with
+// `abort` given, a CTA that finds it set takes no further matrix (those not
+// started keep their done flag at zero).
 struct PersistArgs {
     FusedArgs base;            // outputs, options, jobs and shared-memory offsets
     const int* mm;             // m of each matrix (by id)
@@ -534,7 +545,7 @@ struct PersistArgs {
     const int* order;          // queue of ids
     int count;                 // queue length
     int* head;                 // queue head, zero at launch
-    void* ws;                  // gridDim.x slots of slot_elems elements
+    void* ws;                  // gridDim.x slots of slot_elems elements (global-slot launches)
     long long slot_elems;
     int* done;                 // per-id completion flags (host-mapped memory) or nullptr
     const int* abort;          // nonzero: take no further matrix (host-mapped) or nullptr
@@ -555,12 +566,17 @@ constexpr int persist_min_blocks() {
     return std::is_same<T, double2>::value ? 1 : 2;
 }
 
-template <class T, int NB, int NG, int GT>
-__global__ void __launch_bounds__(NG * GT, persist_min_blocks<T>())
+// On-chip launches keep the on-chip kernel's occupancy (two CTAs per SM for
+// real FP32, else one).
+template <class T, bool OnChip>
+constexpr int persist_blocks() { return OnChip ? fused_min_blocks<T>() : persist_min_blocks<T>(); }
+
+template <class T, int NB, int NG, int GT, bool OnChip>
+__global__ void __launch_bounds__(NG * GT, (min_blocks_for<persist_blocks<T, OnChip>(), NG * GT>()))
 gesvj_persistent_kernel(const PersistArgs p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_mid;
-    T* const slot = static_cast<T*>(p.ws) + (long long)blockIdx.x * p.slot_elems;
+    T* const slot = OnChip ? reinterpret_cast<T*>(smem) : static_cast<T*>(p.ws) + (long long)blockIdx.x * p.slot_elems;
     for (;;) {
         if (threadIdx.x == 0) {
             if (p.abort && *reinterpret_cast<const volatile int*>(p.abort)) {
@@ -579,7 +595,7 @@ gesvj_persistent_kernel(const PersistArgs p) {
         const long long per16 = 16 / (long long)sizeof(T) > 0 ? 16 / (long long)sizeof(T) : 1;
         T* const W = slot;
         T* const Vs = slot + ((long long)a.ldw * a.Np + per16 - 1) / per16 * per16;
-        fused_solve<T, NB, NG, GT, false>(a, mid, W, Vs, smem);
+        fused_solve<T, NB, NG, GT, OnChip>(a, mid, mid, W, Vs, smem);
         if (p.done) __threadfence_system();                // this thread's outputs before the flag
         __syncthreads();                                   // shared scratch reused next
         if (p.done && threadIdx.x == 0) store_release_sys(p.done + mid, 1);

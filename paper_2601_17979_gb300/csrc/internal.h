@@ -18,7 +18,9 @@ struct PersistArgs;
 // working orientation M = max(m, n) rows, N = min(m, n) columns).
 struct MixedArgs {
     int m, n, M, N, trans;
-    const void* A; long long sA; int lda;   // the caller's FP64 / complex128 A
+    const void* A; long long sA; int lda;   // the caller's FP64 / complex128 A (strided), or
+    const void* const* Ap; const int* ldap; // pointer arrays by matrix id, with
+    const int* index;                       // the ids of this launch's matrices
     void* A32;                              // M x N, ld M: FP32 copy of 2^-ex A (or A^H)
     void* V32;                              // N x N, ld N: V of the FP32 solve
     void* V64; void* Vtmp; void* E;         // N x N, ld N, FP64: restored V and scratch
@@ -71,9 +73,10 @@ bsvd_status persistent_with_flags(bsvd_handle h, char t, bool wantU, bool wantV,
     size_t fused_plan_##TAG(int nb, int M, int N, bool needVs, FusedArgs& a, int& nt);  \
     cudaError_t fused_launch_##TAG(int nb, const FusedArgs& a, int grid, size_t smem,   \
                                    cudaStream_t st);                                    \
-    cudaError_t persist_launch_##TAG(int nb, const PersistArgs& p, int grid, int maxN,  \
-                                     cudaStream_t st);                                  \
-    long long persist_slot_##TAG(int nb, int m, int n);
+    cudaError_t persist_launch_##TAG(int nb, bool onchip, size_t wv, const PersistArgs& p, int grid, \
+                                     int maxN, cudaStream_t st);                        \
+    long long persist_slot_##TAG(int nb, int m, int n);                                 \
+    size_t persist_smem_##TAG(int nb, size_t wv, int maxN);
 
 #define BSVD_DECLARE_BLOCKED(TAG)                                                               \
     cudaError_t blocked_run_##TAG(int nb, const BlockedArgs& a, void* work, cudaStream_t st,   \

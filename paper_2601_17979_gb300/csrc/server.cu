@@ -130,8 +130,11 @@ struct bsvd_server_s {
     int device = 0;
     char* arena_base = nullptr;
     Arena* arena = nullptr;
-    int max_inflight = 32, max_batch = 4096, big_k = 256, max_big_batch = 64;
-    std::vector<cudaStream_t> streams;
+    int max_inflight = 32, max_batch = 4096, big_k = 256, max_big_batch = 8, fp64_prec = 0;
+    // per slot two streams: high priority for persistent batches (small
+    // requests), low priority for multi-kernel batches (large ones), so the
+    // block scheduler starts a small request's CTAs before a large batch's
+    std::vector<cudaStream_t> streams, streams_lo;
     std::vector<cudaEvent_t> events;
     std::vector<int*> hflags;      // per slot, host-mapped: info, sweeps, done (max_batch each), abort
     std::vector<int*> dflags;      // the same memory's device addresses
@@ -153,6 +156,7 @@ struct bsvd_server_s {
     long long next_id = 1, submitted = 0, completed = 0, failed = 0, cancelled = 0, launched = 0;
     long long queued = 0, in_flight = 0;
     bool stop = false, paused = false;
+    long long wake_gen = 0;        // bumped (under mu) by every submit, release, pause and cancel
     std::thread worker;
 };
 
@@ -172,25 +176,31 @@ size_t out_bytes(const Request* r) {
     return b;
 }
 
-bsvd_opts batch_opts(const Request* r0, bool persistent) {
+bsvd_opts batch_opts(const bsvd_server_s* s, const Request* r0, bool persistent) {
     bsvd_opts o;
     std::memset(&o, 0, sizeof o);
     o.nb = persistent ? auto_nb(r0->k) : 16;
     o.path = persistent ? BSVD_PATH_PERSISTENT : BSVD_PATH_AUTO;
-    o.flags = persistent ? 0 : 16;   // stop issuing sweeps once the batch has converged
+    // persistent batches keep W and V in global slots (flags bit 9): their
+    // CTAs then take little shared memory, so the CTAs of many batches share
+    // the SMs and a newly admitted batch starts while older ones run;
+    // multi-kernel batches stop issuing sweeps once converged (bit 4, for
+    // the fallback without the device-side loop)
+    o.flags = persistent ? 512 : 16;
+    if (!persistent && (r0->dtype == 'd' || r0->dtype == 'z')) o.prec = s->fp64_prec;
     return o;
 }
 
 // Workspace of a batch: four pointer arrays, then the solver's workspace
 // (0 if the solver cannot plan the batch).
-size_t ws_bytes(bsvd_handle h, const std::vector<Request*>& rs, bool persistent) {
+size_t ws_bytes(const bsvd_server_s* s, bsvd_handle h, const std::vector<Request*>& rs, bool persistent) {
     std::vector<int> mm, nn;
     for (const Request* r : rs) {
         mm.push_back(r->m);
         nn.push_back(r->n);
     }
     const Request* r0 = rs.front();
-    const bsvd_opts o = batch_opts(r0, persistent);
+    const bsvd_opts o = batch_opts(s, r0, persistent);
     size_t w = 0;
     if (bsvd_gesvj_workspace(h, r0->dtype, (int)rs.size(), mm.data(), nn.data(), 0,
                              r0->wantU ? BSVD_JOB_SOME : BSVD_JOB_NONE, r0->wantV ? BSVD_JOB_SOME : BSVD_JOB_NONE,
@@ -226,7 +236,7 @@ bsvd_status launch_impl(bsvd_server_s* s, const Job& bt, int& cuda_err) {
     const int B = (int)bt.reqs.size();
     const Request* r0 = bt.reqs.front();
     const char t = r0->dtype;
-    cudaStream_t st = s->streams[bt.slot];
+    cudaStream_t st = bt.persistent ? s->streams[bt.slot] : s->streams_lo[bt.slot];
     std::vector<const void*> pA(B);
     std::vector<void*> pS(B), pU(B), pV(B);
     std::vector<int> mm(B), nn(B), lda(B), ldu(B), ldv(B);
@@ -255,7 +265,7 @@ bsvd_status launch_impl(bsvd_server_s* s, const Job& bt, int& cuda_err) {
     }
     int* df = s->dflags[bt.slot];
     const int MB = s->max_batch;
-    const bsvd_opts o = batch_opts(r0, bt.persistent);
+    const bsvd_opts o = batch_opts(s, r0, bt.persistent);
     const bsvd_job ju = r0->wantU ? BSVD_JOB_SOME : BSVD_JOB_NONE, jv = r0->wantV ? BSVD_JOB_SOME : BSVD_JOB_NONE;
     bsvd_status rc;
     bsvd_handle h = s->slot_h[bt.slot];
@@ -299,7 +309,7 @@ void launch(bsvd_server_s* s, const Job& bt) {
     const bsvd_status rc = launch_impl(s, bt, cuda_err);
     if (rc != BSVD_OK) {
         cudaGetLastError();
-        cudaStreamSynchronize(s->streams[bt.slot]);   // work already queued
+        cudaStreamSynchronize(bt.persistent ? s->streams[bt.slot] : s->streams_lo[bt.slot]);   // work already queued
         cudaGetLastError();
     }
     s->launch_cuda[bt.slot] = cuda_err;
@@ -405,7 +415,7 @@ void admit(bsvd_server_s* s, std::unique_lock<std::mutex>& lk) {
         bool fits = false, never = false;
         while (take > 0) {
             std::vector<Request*> rs(q.begin(), q.begin() + take);
-            bt.ws_bytes = ws_bytes(s->h, rs, bt.persistent);
+            bt.ws_bytes = ws_bytes(s, s->h, rs, bt.persistent);
             size_t ob = 0;
             for (const Request* r : rs) ob += out_bytes(r);
             if (bt.ws_bytes == 0 ||
@@ -491,9 +501,13 @@ void worker_loop(bsvd_server_s* s) {
         poll_running(s);
         if (!s->stop && !s->paused) admit(s, lk);
         if (s->stop && s->running.empty()) break;
-        if (s->running.empty())
-            s->cv_work.wait(lk, [&] { return s->stop || (!s->paused && any_queued(s)); });
-        else
+        if (s->running.empty()) {
+            // nothing runs: what is queued waits for memory (or was just
+            // admitted), so sleep until a submit, release, pause or cancel
+            // changes something -- never spin holding the mutex
+            const long long g = s->wake_gen;
+            s->cv_work.wait(lk, [&] { return s->stop || (!s->paused && any_queued(s) && s->wake_gen != g); });
+        } else
             s->cv_work.wait_for(lk, std::chrono::microseconds(20));
     }
 }
@@ -530,6 +544,7 @@ bsvd_status submit_at(bsvd_server_s* s, char dtype, int m, int n, const void* A,
         s->queues[key_of(s, r)].push_back(r);
         s->submitted++;
         s->queued++;
+        s->wake_gen++;
     }
     s->cv_work.notify_one();
     *id = r->id;
@@ -562,6 +577,7 @@ bsvd_status release_locked(bsvd_server_s* s, std::map<long long, Request*>::iter
     drop_out(s, r->out);
     s->reqs.erase(it);
     delete r;
+    s->wake_gen++;
     return BSVD_OK;
 }
 
@@ -580,14 +596,15 @@ bsvd_status bsvd_server_create(void* d_arena, size_t arena_bytes, const bsvd_ser
     std::memset(&z, 0, sizeof z);
     if (!opts) opts = &z;
     if (opts->max_inflight < 0 || opts->max_inflight > 64 || opts->max_batch < 0 || opts->big_k < 0 ||
-        opts->max_big_batch < 0)
+        opts->max_big_batch < 0 || (opts->fp64_prec != BSVD_PREC_NATIVE && opts->fp64_prec != BSVD_PREC_MIXED))
         return BSVD_ERR_INVALID;
     bsvd_server_s* s = new (std::nothrow) bsvd_server_s();
     if (!s) return BSVD_ERR_NOMEM;
     s->max_inflight = opts->max_inflight ? opts->max_inflight : 32;
     s->max_batch = opts->max_batch ? opts->max_batch : 4096;
     s->big_k = opts->big_k ? opts->big_k : 256;
-    s->max_big_batch = opts->max_big_batch ? opts->max_big_batch : 64;
+    s->max_big_batch = opts->max_big_batch ? opts->max_big_batch : 8;
+    s->fp64_prec = opts->fp64_prec;
     s->arena_base = static_cast<char*>(d_arena);
     bsvd_status rc = BSVD_OK;
     if (cudaGetDevice(&s->device) != cudaSuccess) rc = BSVD_ERR_CUDA;
@@ -597,6 +614,7 @@ bsvd_status bsvd_server_create(void* d_arena, size_t arena_bytes, const bsvd_ser
         if (!s->arena) rc = BSVD_ERR_NOMEM;
     }
     s->streams.assign(s->max_inflight, nullptr);
+    s->streams_lo.assign(s->max_inflight, nullptr);
     s->events.assign(s->max_inflight, nullptr);
     s->hflags.assign(s->max_inflight, nullptr);
     s->dflags.assign(s->max_inflight, nullptr);
@@ -615,7 +633,10 @@ bsvd_status bsvd_server_create(void* d_arena, size_t arena_bytes, const bsvd_ser
     for (int k = 0; k < s->max_inflight && rc == BSVD_OK; ++k) {
         void* hp = nullptr;
         void* dp = nullptr;
-        if (cudaStreamCreateWithFlags(&s->streams[k], cudaStreamNonBlocking) != cudaSuccess ||
+        int lo = 0, hi = 0;
+        if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&s->streams[k], cudaStreamNonBlocking, hi) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&s->streams_lo[k], cudaStreamNonBlocking, lo) != cudaSuccess ||
             cudaEventCreateWithFlags(&s->events[k], cudaEventDisableTiming) != cudaSuccess ||
             cudaHostAlloc(&hp, sizeof(int) * flag_ints(s), cudaHostAllocMapped) != cudaSuccess) {
             rc = BSVD_ERR_CUDA;
@@ -632,6 +653,7 @@ bsvd_status bsvd_server_create(void* d_arena, size_t arena_bytes, const bsvd_ser
         cudaGetLastError();
         for (int k = 0; k < s->max_inflight; ++k) {
             if (s->streams[k]) cudaStreamDestroy(s->streams[k]);
+            if (s->streams_lo[k]) cudaStreamDestroy(s->streams_lo[k]);
             if (s->events[k]) cudaEventDestroy(s->events[k]);
             if (s->hflags[k]) cudaFreeHost(s->hflags[k]);
         }
@@ -800,6 +822,7 @@ bsvd_status bsvd_server_pause(bsvd_server s, int paused) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->paused = paused != 0;
+        s->wake_gen++;
     }
     s->cv_work.notify_one();
     return BSVD_OK;
@@ -834,6 +857,7 @@ bsvd_status bsvd_server_destroy(bsvd_server s) {
     for (auto& kv : s->reqs) delete kv.second;
     for (int k = 0; k < s->max_inflight; ++k) {
         if (s->streams[k]) cudaStreamDestroy(s->streams[k]);
+        if (s->streams_lo[k]) cudaStreamDestroy(s->streams_lo[k]);
         if (s->events[k]) cudaEventDestroy(s->events[k]);
         if (s->hflags[k]) cudaFreeHost(s->hflags[k]);
     }

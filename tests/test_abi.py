@@ -209,3 +209,26 @@ def test_split_workspace_query(L):
     a = n.value
     assert L.bsvd_gesvj_workspace(h, b"c", 2, small, small, 0, 1, 1, ctypes.byref(split), ctypes.byref(n)) == 0
     assert n.value == a                          # nothing reaches the multi-kernel path
+
+
+def test_persistent_plan_host_logic():
+    """The per-matrix decision of a persistent batch, computed on the host
+    (no GPU needed): the block width follows min(m, n) (>= 48: 16, >= 12: 8,
+    else 4) unless opts.nb is given; small matrices keep W and V in shared
+    memory, large ones in global slots; empty matrices are not planned;
+    complex64 with flags bit 6 sends min(m, n) >= 128 to the multi-kernel
+    batch."""
+    import numpy as np
+    import paper_2601_17979_gb300 as bsvd
+    shapes = [(8, 8), (30, 20), (100, 64), (512, 400), (0, 5), (12, 300), (47, 47)]
+    nb, where, launches = bsvd.persistent_plan("s", shapes)
+    assert nb.tolist() == [4, 8, 16, 16, 0, 8, 8]
+    assert where[0] == 1 and where[1] == 1 and where[2] == 1 and where[3] == 0 and where[4] == -1
+    assert launches == len({(int(a), int(b)) for a, b in zip(nb, where) if b >= 0})
+    nb2, where2, _ = bsvd.persistent_plan("s", shapes, nb=8)
+    assert all(x == 8 for x, w in zip(nb2, where2) if w >= 0)
+    _, where3, launches3 = bsvd.persistent_plan("s", shapes, flags=bsvd.FLAG_NO_ONCHIP)
+    assert set(where3.tolist()) == {0, -1}
+    _, where4, _ = bsvd.persistent_plan("c", [(300, 150), (40, 30), (128, 128)], flags=bsvd.FLAG_SPLIT_LARGE)
+    assert where4.tolist()[0] == 2 and where4.tolist()[2] == 2 and where4.tolist()[1] == 1
+    assert np.all(nb >= 0)

@@ -66,9 +66,10 @@ def test_single_rank_is_identity():
 
 
 def test_uneven_launch_count():
-    """The uneven step's launch claim: one persistent launch per type, and
-    for the complex64 split (min(m, n) >= 128) the multi-kernel batch's load,
-    4 * ceil(max sweeps / 4) sweeps of 3 (L_max - 1) + 1 kernels and three
+    """The uneven step's launch claim: one persistent launch per segment of
+    each type (from the plan), and for the complex64 split (the plan's
+    where = 2) the multi-kernel batch's load, max-sweeps sweeps of
+    3 (L_max - 1) + 2 kernels (the device stops the loop) and three
     finalisation kernels."""
     from types import SimpleNamespace
     f32, c64 = np.dtype(np.float32), np.dtype(np.complex64)
@@ -77,9 +78,12 @@ def test_uneven_launch_count():
                     np.zeros((200, 130), np.complex64)]}
     res = {f32: SimpleNamespace(sweeps=torch.tensor([12])),
            c64: SimpleNamespace(sweeps=torch.tensor([20, 13, 9]))}
-    # complex64 split: n up to 300 -> l = 19 blocks, L = 20; 13 sweeps -> 16 issued
-    per_step = 2 + 1 + 16 * (3 * 19 + 1) + 3
-    assert bench.uneven_launches(groups, res, steps=1) == per_step
-    assert bench.uneven_launches(groups, res, steps=3) == 3 * per_step
+    plans = {f32: (np.array([16]), np.array([0]), 1),
+             c64: (np.array([8, 16, 16]), np.array([1, 2, 2]), 1)}
+    # complex64 split: n up to 300 -> l = 19 blocks, L = 20; 13 sweeps issued
+    per_step = 2 + 1 + 13 * (3 * 19 + 2) + 3
+    assert bench.uneven_launches(groups, res, plans, steps=1) == per_step
+    assert bench.uneven_launches(groups, res, plans, steps=3) == 3 * per_step
     res_small = {f32: res[f32], c64: SimpleNamespace(sweeps=torch.tensor([20]))}
-    assert bench.uneven_launches({f32: groups[f32], c64: groups[c64][:1]}, res_small, steps=2) == 4
+    plans_small = {f32: plans[f32], c64: (np.array([8]), np.array([1]), 1)}
+    assert bench.uneven_launches({f32: groups[f32], c64: groups[c64][:1]}, res_small, plans_small, steps=2) == 4

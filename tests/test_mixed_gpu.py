@@ -54,7 +54,7 @@ def test_mixed96_clustered(half):
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.complex128])
-@pytest.mark.parametrize("m,n", [(64, 48), (48, 64), (33, 33), (200, 40), (9, 3)])
+@pytest.mark.parametrize("m,n", [(64, 48), (48, 64), (33, 33), (200, 40), (9, 3), (260, 140), (140, 260)])
 def test_mixed_random_shapes(dtype, m, n):
     rng = np.random.default_rng(m * 7 + n)
     mats = [rng.standard_normal((m, n)) + (1j * rng.standard_normal((m, n)) if dtype == np.complex128 else 0)
@@ -93,3 +93,32 @@ def test_mixed_variants_meet_fp64_bounds(flags):
     for lo, hi in ((0, 12), (12, 14)):
         S, Uo, Vo, info, sw = run(mats[lo:hi], nb=16, prec="mixed", flags=flags)
         check(mats[lo:hi], S, Uo, Vo, info, ref["S"][lo:hi], f"flags {flags}")
+
+
+@pytest.mark.parametrize("path", ["auto", "persistent"])
+@pytest.mark.parametrize("dtype", [np.float64, np.complex128])
+def test_mixed_pointer_array_mixed_shapes(path, dtype):
+    """Mixed precision on a pointer-array batch of several shapes (grouped by
+    shape, inputs and outputs through the pointer arrays, wide shapes solved
+    as A^H): every result meets the FP64 bounds against the oracle, and each
+    equals the strided mixed call on its own shape group bitwise."""
+    rng = np.random.default_rng(61)
+    shapes = [(64, 48), (48, 64), (64, 48), (130, 40), (33, 33), (0, 3), (64, 48), (40, 130)]
+    cplx = dtype == np.complex128
+    mats = [(rng.standard_normal(s) + (1j * rng.standard_normal(s) if cplx else 0)).astype(dtype) for s in shapes]
+    T = [torch.from_numpy(np.asfortranarray(x)).cuda() for x in mats]
+    r = bsvd.gesvj_batched(T, prec="mixed", path=path)
+    torch.cuda.synchronize()
+    info = r.info.cpu().numpy()
+    assert (info == 0).all(), info
+    for k, (A, s) in enumerate(zip(mats, shapes)):
+        if min(s) == 0:
+            continue
+        ref = oracle.gesvj(A, tol=30 * U)
+        check([A], [r.S[k].cpu().numpy()], [r.U[k].cpu().numpy()], [r.V[k].cpu().numpy()], [0], [ref["S"]],
+              f"{path} {s}")
+    same = [k for k, s in enumerate(shapes) if s == (64, 48)]
+    Sg, Ug, Vg, ig, wg = run([mats[k] for k in same], prec="mixed")
+    for j, k in enumerate(same):
+        assert np.array_equal(r.S[k].cpu().numpy(), Sg[j]) and np.array_equal(r.U[k].cpu().numpy(), Ug[j])
+        assert np.array_equal(r.V[k].cpu().numpy(), Vg[j]) and int(r.sweeps[k]) == wg[j]

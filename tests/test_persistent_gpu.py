@@ -64,16 +64,18 @@ def test_mixed_shapes_and_edges(dtype):
         assert checks.violations(meas, u) == [], (i, meas)
 
 
+@pytest.mark.parametrize("flags", [0, bsvd.FLAG_NO_ONCHIP])
 @pytest.mark.parametrize("dtype", [np.float32, np.float64, np.complex64, np.complex128])
-def test_persistent_equals_on_chip_bitwise(dtype):
+def test_persistent_equals_on_chip_bitwise(dtype, flags):
     """Both kernels run the same per-matrix code (the layout of each matrix
     comes from its own shape, the rotations' roundings are fixed by explicit
-    FMAs), so the persistent launch gives the on-chip kernel's bits."""
+    FMAs), so the persistent launch gives the on-chip kernel's bits, with W
+    and V in shared memory (these shapes fit) or in global slots (bit 9)."""
     rng = np.random.default_rng(22)
     shapes = [(48, 32), (32, 48), (100, 64), (20, 20)]
     cplx = np.issubdtype(dtype, np.complexfloating)
     mats = [(rng.standard_normal(s) + (1j * rng.standard_normal(s) if cplx else 0)).astype(dtype) for s in shapes]
-    S1, U1, V1, i1, w1 = run_batched(mats, path="persistent", nb=8)
+    S1, U1, V1, i1, w1 = run_batched(mats, path="persistent", nb=8, flags=flags)
     S2, U2, V2, i2, w2 = run_batched(mats, path="fused", nb=8)
     assert (i1 == 0).all() and (i2 == 0).all()
     assert np.array_equal(w1, w2)
@@ -143,3 +145,74 @@ def test_split_large_uneven_sample_and_jobs(cplx):
     assert U2 is None and V2 is None and (i2 == 0).all()
     for i in range(len(mats)):
         assert np.abs(S2[i] - S[i]).max() <= 50 * min(mats[i].shape) * checks.U32 * S[i][0]
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.complex64, np.float64])
+def test_segments_per_shape_block_width(dtype):
+    """A batch whose shapes take different block widths (4, 8, 16) and both
+    homes of W and V (shared memory, global slot) runs as several persistent
+    launches; each matrix gets the bits of the same matrix solved alone with
+    its planned block width, and meets the bounds against the oracle."""
+    rng = np.random.default_rng(41)
+    shapes = [(8, 8), (30, 20), (9, 5), (100, 64), (420, 200), (64, 130), (25, 14), (260, 180)]
+    cplx = np.issubdtype(dtype, np.complexfloating)
+    mats = [(rng.uniform(-1, 1, s) + (1j * rng.uniform(-1, 1, s) if cplx else 0)).astype(dtype) for s in shapes]
+    nb, where, launches = bsvd.persistent_plan(dtype, shapes)
+    assert launches >= 3 and set(where.tolist()) == {0, 1}, (nb, where)
+    S, U, V, info, sw = run_batched(mats, path="persistent")
+    assert (info == 0).all(), info
+    u = checks.unit_roundoff(dtype)
+    for k, A in enumerate(mats):
+        S1, U1, V1, i1, w1 = run_batched([A], path="persistent", nb=int(nb[k]))
+        assert sw[k] == w1[0] and np.array_equal(S[k], S1[0]), k
+        assert np.array_equal(U[k], U1[0]) and np.array_equal(V[k], V1[0]), k
+        meas = checks.measures(A, S[k], U[k], V[k], oracle.gesvj(A)["S"])
+        assert checks.violations(meas, u) == [], (k, A.shape, meas)
+
+
+def test_autotune_batched_buckets_are_followed():
+    """Per-bucket autotuning of a mixed-shape batch: every bucket gets a
+    block width among 4, 8, 16 whose time is the smallest measured; the
+    persistent plan then uses each bucket's width, and the batch still
+    meets the bounds.  Run on its own host thread, whose library handle
+    (and so its tuning table) no other test shares."""
+    import threading
+    out = {}
+
+    def body():
+        try:
+            mats = synth.matrices("uneven", range(0, 120, 2))          # FP32 sample of the workload
+            T = [torch.from_numpy(np.asfortranarray(x)).cuda() for x in mats]
+            table = bsvd.autotune_batched(T, sample=8)
+            nb, where, _ = bsvd.persistent_plan(np.float32, [x.shape for x in mats])
+            r = bsvd.gesvj_batched(T, path="persistent")
+            torch.cuda.synchronize()
+            out.update(mats=mats, table=table, nb=nb, r=r)
+        except Exception as e:                                     # reported by the main thread
+            out["error"] = e
+
+    th = threading.Thread(target=body)
+    th.start()
+    th.join()
+    assert "error" not in out, out.get("error")
+    table, mats, nb, r = out["table"], out["mats"], out["nb"], out["r"]
+    assert table and all(b["nb"] in (4, 8, 16) for b in table)
+    for b in table:
+        done = {w: t for w, t in b["ms"].items() if t >= 0}
+        assert b["ms"][b["nb"]] == min(done.values()), b
+    chosen = {(b["M"], b["N"]): b["nb"] for b in table}
+
+    def p2(x):
+        p = 1
+        while p < x:
+            p *= 2
+        return p
+    for k, A in enumerate(mats):
+        m, n = A.shape
+        assert nb[k] == chosen[(p2(max(m, n)), p2(min(m, n)))], (A.shape, nb[k])
+    info = r.info.cpu().numpy()
+    assert (info == 0).all()
+    ref = oracle.gesvj(mats)
+    for k, A in enumerate(mats):
+        meas = checks.measures(A, r.S[k].cpu().numpy(), r.U[k].cpu().numpy(), r.V[k].cpu().numpy(), ref["S"][k])
+        assert checks.violations(meas, checks.U32) == [], (k, A.shape, meas)

@@ -127,18 +127,19 @@ def test_requests_retire_before_their_batch_ends():
 
 
 def test_memory_budget_admission():
-    """A 4 MiB arena serves 60 requests in small batches, never above budget;
-    a request that cannot fit even alone fails with BSVD_ERR_WORKSPACE."""
+    """A 2 MiB arena serves 60 requests (66 KB of outputs each) in several
+    batches, never above budget; a request that cannot fit even alone fails
+    with BSVD_ERR_WORKSPACE."""
     rng = np.random.default_rng(15)
     mats = [rand(rng, 64, 64, "d") for _ in range(60)]
-    with bsvd.Server(4 * MiB) as srv:
+    with bsvd.Server(2 * MiB) as srv:
         ids = [srv.submit(pinned(A)) for A in mats]
         for A, r in zip(mats, ids):
             res = srv.fetch(r)
             if r % 10 == 0:
                 check_result(A, res, "budget")
         st = srv.stats()
-        assert st["completed"] == 60 and st["arena_peak"] <= 4 * MiB and st["batches"] > 1
+        assert st["completed"] == 60 and st["arena_peak"] <= 2 * MiB and st["batches"] > 1
         huge = srv.submit(pinned(rand(rng, 1024, 1024, "d")))
         with pytest.raises(bsvd.BsvdError, match="WORKSPACE"):
             srv.wait(huge, timeout=30)
@@ -249,3 +250,17 @@ def test_concurrent_multi_kernel_batches():
         for A, r in zip(mats, ids):
             check_result(A, srv.fetch(r), f"{A.dtype} {A.shape}")
         assert srv.stats()["failed"] == 0
+
+
+def test_fp64_mixed_precision_for_large_requests():
+    """With fp64_prec = mixed the server solves FP64 and complex128 requests
+    on the multi-kernel path (min(m, n) > big_k) by FP32 sweeps and FP64
+    polish: the results meet the FP64 bounds; smaller FP64 requests and
+    other types are unaffected."""
+    rng = np.random.default_rng(71)
+    cases = [(rand(rng, 70, 50, "d"), "d"), (rand(rng, 50, 70, "d"), "d"), (rand(rng, 66, 40, "z"), "z"),
+             (rand(rng, 70, 50, "d"), "d"), (rand(rng, 30, 20, "d"), "d"), (rand(rng, 60, 45, "s"), "s")]
+    with bsvd.Server(256 * MiB, big_k=32, fp64_prec="mixed") as srv:
+        ids = [srv.submit(pinned(A)) for A, _ in cases]
+        for (A, t), r in zip(cases, ids):
+            check_result(A, srv.fetch(r), f"mixed server {t} {A.shape}")
