@@ -556,6 +556,19 @@ def summarize_stream(tr, ids, t0, t_arrivals, t_stop, rec, idx, before, at_end, 
            "drained": bool(final["queued"] == 0 and final["running"] == 0),
            "drain_s": t_stop - t_arrivals, "info_nonzero": int((rec["info"][ok] != 0).sum()),
            "arena_peak_gb": final["arena_peak"] / 1e9}
+    # latency by request class: small (k <= 64), medium (64 < k <= 256, the
+    # persistent batches), large (k > 256, the multi-kernel batches), by type
+    if n_done:
+        kk = np.minimum(m, n)
+        dts = tr["dtype"][idx[ok]]
+        classes = {}
+        for cname, sel in (("small", kk <= 64), ("medium", (kk > 64) & (kk <= 256)), ("large", kk > 256)):
+            for t in ("s", "d", "c"):
+                sl = sel & (dts == t)
+                if sl.any():
+                    classes[f"{cname}_{t}"] = {"n": int(sl.sum()), "p50": float(np.percentile(lat[sl], 50)),
+                                               "p99": float(np.percentile(lat[sl], 99))}
+        out["latency_by_class_ms"] = classes
     bad = (rec["status"] != 0) & (rec["status"] != -7)
     if bad.any():
         codes, counts = np.unique(rec["status"][bad], return_counts=True)
@@ -585,7 +598,8 @@ def run_serving(args, rank, world, local):
     rate = args.rate or cfg["rate"]
     seconds = args.seconds or cfg["seconds"]
     pool = {}
-    srv = bsvd.Server(int(args.arena_gb * 1e9), max_inflight=32, fp64_prec=args.fp64_prec)
+    srv = bsvd.Server(int(args.arena_gb * 1e9), max_inflight=32, fp64_prec=args.fp64_prec,
+                      big_flags=args.big_flags, max_big_batch=args.max_big_batch)
     # warm-up: a short low-rate stream (first launches set kernel attributes)
     for _ in range(max(1, args.warmup)):
         serve_stream(srv, 500.0, 0.2, 30.0, 1000 + rank, pool)
@@ -601,7 +615,8 @@ def run_serving(args, rank, world, local):
         s_ = summarize_stream(*rr, args.sweep_seconds)
         sweep.append({"rate_rps": lam, "p50_ms": s_["latency_ms"]["p50"], "p99_ms": s_["latency_ms"]["p99"],
                       "throughput_rps": s_["throughput_rps"], "completed": s_["completed"],
-                      "submitted": s_["submitted"], "drained": s_["drained"]})
+                      "submitted": s_["submitted"], "drained": s_["drained"],
+                      "by_class_ms": s_.get("latency_by_class_ms")})
     batches = srv.stats()["batches"]
     srv.close()
     value = sum_over_ranks(main["throughput_rps"], dist, dev)
@@ -615,6 +630,7 @@ def run_serving(args, rank, world, local):
                                    "30% FP64 / 20% complex64, kappa log-uniform 1e2..1e6, logrand sigma, "
                                    "Haar factors; inputs from a pool of 2 matrices per (bin, shape, type)",
                        "arena_gb": args.arena_gb, "max_inflight": 32, "jobs": "U, Sigma, V",
+                       "big_flags": args.big_flags, "max_big_batch": args.max_big_batch or 8,
                        "fp64_prec": args.fp64_prec + " (FP64 / complex128 requests above 256 columns)",
                        "results": "left in the arena and released on completion (not copied back)",
                        "l2": "inputs read once from page-locked host memory"},
@@ -1075,6 +1091,8 @@ def main():
     ap.add_argument("--seconds", type=float, default=0.0, help="serving: stream length (default 10 s)")
     ap.add_argument("--drain", type=float, default=10.0, help="serving: seconds to drain after arrivals")
     ap.add_argument("--arena-gb", type=float, default=40.0, help="serving: device-memory budget")
+    ap.add_argument("--big-flags", type=int, default=0, help="serving: flags added to multi-kernel batches")
+    ap.add_argument("--max-big-batch", type=int, default=0, help="serving: requests per multi-kernel batch")
     ap.add_argument("--fp64-prec", default="mixed", choices=["native", "mixed"],
                     help="serving: precision path of large FP64 requests (FP64 accuracy either way)")
     ap.add_argument("--sweep-rates", type=float, nargs="*", default=[25, 50, 100, 200])

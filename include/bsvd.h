@@ -129,15 +129,19 @@ typedef struct {
                           types ignore it.  With bit 4 the call returns once those
                           matrices have converged.  Workspace: bsvd_gesvj_workspace with
                           the same options;
-                          bit 7: real FP32 with nb = 8 or 16 forms the Gram blocks and
-                          the rotation updates on the FMA pipes (register tiles)
-                          instead of the tensor cores (split-TF32 mma, FP32 accuracy);
+                          bit 7: real FP32 with nb = 8 or 16 (and complex64 on the
+                          multi-kernel path) forms the Gram blocks and the rotation
+                          updates on the FMA pipes instead of the tensor cores
+                          (split-TF32 mma, FP32 accuracy);
                           bit 8: single-precision data (and the FP32 sweeps of MIXED)
                           take the pair test and the rotation (Eq. sin-cos) in FP64,
                           rounded once to FP32;
                           bit 9: BSVD_PATH_PERSISTENT keeps every matrix in a global
                           workspace slot (no shared-memory segments);
-                          bit 10: with bit 6, real FP32 batches split the same way      */
+                          bit 10: with bit 6, real FP32 batches split the same way;
+                          bit 11: the masked multi-kernel path replays a one-sweep
+                          graph from the host (bit 4 applies) instead of the
+                          device-side conditional loop                                  */
     int prec;          /* bsvd_prec; MIXED only for d/z.  Pointer-array batches run MIXED per
                           shape group (also with BSVD_PATH_PERSISTENT), reading A and
                           writing S, U, V through the pointer arrays                     */
@@ -387,7 +391,9 @@ typedef struct {
     int fp64_prec;      /* bsvd_prec of FP64 / complex128 requests on the multi-kernel path
                            (min(m, n) > big_k): BSVD_PREC_NATIVE (0, default) or
                            BSVD_PREC_MIXED (FP32 sweeps + FP64 polish, FP64 accuracy)      */
-    int reserved[3];    /* zero                                                                  */
+    int big_flags;      /* further bsvd_opts.flags bits for multi-kernel batches (which always
+                           run with bits 4 and 11: a host-replayed one-sweep graph)        */
+    int reserved[2];    /* zero                                                                  */
 } bsvd_server_opts;
 
 double bsvd_server_clock(void);

@@ -26,7 +26,7 @@ PATHS = {"auto": 0, "fused": 1, "plain": 2, "blocked": 3, "persistent": 4}
 PATH_NAMES = {v: k for k, v in PATHS.items()}
 FLAG_NO_V_CORRECTION, FLAG_TWO_STAGE, FLAG_NO_MASKS, FLAG_NO_GRAPH, FLAG_SYNC_CHECK, FLAG_QR = 1, 2, 4, 8, 16, 32
 FLAG_SPLIT_LARGE = 64
-FLAG_F32_FFMA, FLAG_WIDE_ANGLES, FLAG_NO_ONCHIP, FLAG_SPLIT_F32 = 128, 256, 512, 1024
+FLAG_F32_FFMA, FLAG_WIDE_ANGLES, FLAG_NO_ONCHIP, FLAG_SPLIT_F32, FLAG_HOST_LOOP = 128, 256, 512, 1024, 2048
 DTYPES = {torch.float32: "s", torch.float64: "d", torch.complex64: "c", torch.complex128: "z"}
 REAL = {torch.float32: torch.float32, torch.float64: torch.float64,
         torch.complex64: torch.float32, torch.complex128: torch.float64}
@@ -60,7 +60,8 @@ class BsvdError(RuntimeError):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("max_inflight", ctypes.c_int), ("max_batch", ctypes.c_int), ("big_k", ctypes.c_int),
-                ("max_big_batch", ctypes.c_int), ("fp64_prec", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("max_big_batch", ctypes.c_int), ("fp64_prec", ctypes.c_int), ("big_flags", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class Opts(ctypes.Structure):
@@ -534,7 +535,7 @@ class Server:
     """
 
     def __init__(self, arena_bytes: int, *, max_inflight: int = 0, max_batch: int = 0, big_k: int = 0,
-                 max_big_batch: int = 0, fp64_prec="native", device=None):
+                 max_big_batch: int = 0, fp64_prec="native", big_flags: int = 0, device=None):
         self.lib = load()
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.device = dev
@@ -543,6 +544,7 @@ class Server:
         o.max_inflight, o.max_batch, o.big_k = int(max_inflight), int(max_batch), int(big_k)
         o.max_big_batch = int(max_big_batch)
         o.fp64_prec = PRECS[fp64_prec] if isinstance(fp64_prec, str) else int(fp64_prec)
+        o.big_flags = int(big_flags)
         srv = ctypes.c_void_p()
         with torch.cuda.device(dev):
             st = self.lib.bsvd_server_create(self.arena.data_ptr(), self.arena.numel(), ctypes.byref(o),

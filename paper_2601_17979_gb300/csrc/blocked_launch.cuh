@@ -128,7 +128,8 @@ cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stag
                          a.N * ((int)sizeof(R) + 4) + 16;
     // J, column stride up to 2nb + 1; real FP32 J's split-TF32 fragments
     const int upd_smem = std::max(TWO * (TWO + 1) * (int)sizeof(T),
-                                  std::is_same<T, float>::value ? j_fragment_bytes<NB>() : 0);
+                                  std::is_same<T, float>::value    ? j_fragment_bytes<NB>()
+                                  : std::is_same<T, float2>::value ? jc_fragment_bytes<NB>() : 0);
     if ((e = allow_dynamic_smem<blk_heevj<T, NB, GT>>()) != cudaSuccess ||
         (e = allow_dynamic_smem<blk_finalize<T>>()) != cudaSuccess ||
         (e = allow_dynamic_smem<blk_update_fused<T, NB>>()) != cudaSuccess ||
@@ -157,8 +158,13 @@ cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stag
             if constexpr (std::is_same<T, float>::value && (NB == 8 || NB == 16)) {
                 if (a.flags & 128) blk_gram_f32<NB><<<gpair, kBlkThreads, 0, s>>>(a, r);
                 else blk_gram_f32_tc<NB><<<gpair, kBlkThreads, 0, s>>>(a, r);
-            } else if constexpr (std::is_same<T, float>::value && NB >= 8)
+            } else if constexpr (std::is_same<T, float>::value && NB >= 8) {
                 blk_gram_f32<NB><<<gpair, kBlkThreads, 0, s>>>(a, r);
+            } else if constexpr (std::is_same<T, float2>::value && (NB == 8 || NB == 16)) {
+                // complex64: the tensor cores (flags bit 7: the FMA pipes)
+                if (a.flags & 128) blk_gram<T, NB><<<gpair, kBlkThreads, 0, s>>>(a, r);
+                else blk_gram_c64_tc<NB><<<gpair, kBlkThreads, 0, s>>>(a, r);
+            }
             else
                 blk_gram<T, NB><<<gpair, kBlkThreads, 0, s>>>(a, r);
             blk_heevj<T, NB, GT><<<gpair, GT, heevj_smem, s>>>(a, r);
@@ -184,7 +190,7 @@ cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stag
             if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
             if (!any) break;
         }
-    } else if (capture && (e = blk_run_while(a, st, capture, sweep)) != cudaErrorNotSupported) {
+    } else if (capture && !(a.flags & 2048) && (e = blk_run_while(a, st, capture, sweep)) != cudaErrorNotSupported) {
         // the sweep loop ran (or failed) as one graph with a device-side loop
         if (e != cudaSuccess) return e;
     } else {

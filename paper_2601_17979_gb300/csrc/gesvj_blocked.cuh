@@ -19,6 +19,7 @@
 
 #include "blocked_layout.h"
 #include "jacobi_common.cuh"
+#include "tc_c64.cuh"
 #include "tc_f32.cuh"
 
 namespace bsvd {
@@ -185,6 +186,72 @@ __global__ void __launch_bounds__(kBlkThreads) blk_gram_f32_tc(const BlockedArgs
             if (rr > cc) continue;                          // lower entries: the mirror of an upper one
             G[rr + cc * TWO] = x;
             G[cc + rr * TWO] = x;
+        }
+}
+
+// ---- S2, complex64 on the tensor cores (nb = 8, 16) ------------------------------
+// As blk_gram_f32_tc with the panel's real and imaginary parts staged as two
+// planes; each 16 x 16 block of G = P^H P is Re = Pr^T Pr + Pi^T Pi and
+// Im = Pr^T Pi - Pi^T Pr (tc_c64.cuh), the warps' partial blocks summed in
+// warp order, the upper entries written and mirrored (conjugate), the
+// diagonal real.
+template <int NB>
+__global__ void __launch_bounds__(kBlkThreads) blk_gram_c64_tc(const BlockedArgs a, int r) {
+    constexpr int TWO = 2 * NB, NT = kBlkThreads, NW = NT / 32, NBLK = TWO / 16, NB2 = NBLK * NBLK;
+    constexpr int WPB = NW / NB2;
+    static_assert(NW % NB2 == 0, "warps per Gram block");
+    constexpr int KC = kGramChunk, KP = KC + 4;
+    __shared__ __align__(16) float2 P[KP * TWO];
+    __shared__ float red[NW * 32 * 16];
+    const int b = blockIdx.x, q = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (blk_skip(a, b)) return;
+    const BlkShape sh = blk_shape(a, b);
+    int bi, bj;
+    if (!blk_pair(sh, r, q, bi, bj)) return;
+    const float2* W = static_cast<const float2*>(a.W) + sh.oW;
+    const int M = sh.M;
+    const int blk = warp % NB2, sub = warp / NB2, bm = blk / NBLK, bn = blk % NBLK;
+    float re[2][4], im[2][4];
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) re[j][i] = im[j][i] = 0.f;
+    for (int k0 = 0; k0 < M; k0 += KC) {
+        const int kc = min(KC, M - k0);
+        for (int e = tid; e < KC * TWO; e += NT) {
+            const int kk = e % KC, c = e / KC;
+            const int col = c < NB ? bi * NB + c : bj * NB + (c - NB);
+            P[kk + c * KP] = kk < kc ? W[k0 + kk + (long long)col * M] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        gram_c64_block_acc<NB>(P, KP, kc, 0, NB, bm, bn, sub, WPB, lane, re, im);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            red[(warp * 32 + lane) * 16 + 4 * j + i] = re[j][i];
+            red[(warp * 32 + lane) * 16 + 8 + 4 * j + i] = im[j][i];
+        }
+    __syncthreads();
+    if (sub != 0) return;
+    float2* G = static_cast<float2*>(a.G) + sh.oG + (long long)q * TWO * TWO;
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float xr = red[(blk * 32 + lane) * 16 + 4 * j + i], xi = red[(blk * 32 + lane) * 16 + 8 + 4 * j + i];
+            for (int s2 = 1; s2 < WPB; ++s2) {
+                xr += red[((blk + s2 * NB2) * 32 + lane) * 16 + 4 * j + i];
+                xi += red[((blk + s2 * NB2) * 32 + lane) * 16 + 8 + 4 * j + i];
+            }
+            const int rr = 16 * bm + g + 8 * (i >> 1), cc = 16 * bn + 8 * j + 2 * t + (i & 1);
+            if (rr > cc) continue;                          // lower entries: the mirror of an upper one
+            if (rr == cc) xi = 0.f;                         // Hermitian: a real diagonal
+            G[rr + cc * TWO] = make_float2(xr, xi);
+            G[cc + rr * TWO] = make_float2(xr, -xi);
         }
 }
 
@@ -390,6 +457,23 @@ __global__ void __launch_bounds__(kUpdRows) blk_update_fused(const BlockedArgs a
             }
         return;
     }
+    if constexpr (std::is_same<T, float2>::value && (NB == 8 || NB == 16))
+      if (!(a.flags & 128)) {
+        // complex64 on the tensor cores: 16-row tiles of W, then of V, as
+        // real split-TF32 products of the parts (tc_c64.cuh)
+        uint4* Jf = reinterpret_cast<uint4*>(smem_js);
+        jc_fragments<NB, kUpdRows, TWO>(Jg, Jf, tid);
+        __syncthreads();
+        const int tw = (sh.M + 15) / 16, tt = tw + (sh.N + 15) / 16, warp = tid >> 5, lane = tid & 31;
+        float2* Wm = static_cast<float2*>(a.W) + sh.oW;
+        float2* Vm = static_cast<float2*>(a.Vw) + sh.oV;
+        for (int base = blockIdx.z * (kUpdRows / 16); base < tt; base += gridDim.z * (kUpdRows / 16))
+            for (int tile = base + warp; tile < min(tt, base + kUpdRows / 16); tile += kUpdRows / 32) {
+                if (tile < tw) update_rows_c64_mma<NB>(Wm, sh.M, sh.M, 16 * tile, bi * NB, bj * NB, Jf, lane);
+                else           update_rows_c64_mma<NB>(Vm, sh.N, sh.N, 16 * (tile - tw), bi * NB, bj * NB, Jf, lane);
+            }
+        return;
+      }
     if constexpr (std::is_same<T, float2>::value && NB <= 16) {
         // complex64: 4 rows x 2nb/4 columns per thread.  The four lanes of a
         // quad share 4 rows (rs, rs + 32, ...) and take columns cg, cg + 4,

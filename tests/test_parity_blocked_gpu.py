@@ -183,3 +183,16 @@ def test_blocked_fp32_tensor_core_and_ffma(flags, m, n, nb):
     S, U, V, info, sw = run_gpu(mats, nb=nb, path="blocked", flags=flags)
     ref = oracle.gesvj(mats)
     check(mats, S, U, V, info, ref["S"], f"flags {flags} {m}x{n}")
+
+
+@pytest.mark.parametrize("flags", [0, bsvd.FLAG_F32_FFMA, bsvd.FLAG_WIDE_ANGLES])
+@pytest.mark.parametrize("m,n,nb", [(200, 150, 16), (257, 33, 8), (150, 260, 16), (130, 130, 16)])
+def test_blocked_complex64_tensor_core_and_ffma(flags, m, n, nb):
+    """The multi-kernel complex64 Gram and update as real split-TF32 products
+    of the real and imaginary parts (default), on the FMA pipes (flags bit
+    7), and with FP64 rotations (bit 8): bounds against the oracle."""
+    rng = np.random.default_rng(m * 5 + n + nb + flags)
+    mats = [(rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))).astype(np.complex64) for _ in range(3)]
+    S, U, V, info, sw = run_gpu(mats, nb=nb, path="blocked", flags=flags)
+    ref = oracle.gesvj(mats)
+    check(mats, S, U, V, info, ref["S"], f"c64 flags {flags} {m}x{n}")
