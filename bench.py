@@ -53,14 +53,13 @@ PEAK_FP32 = 152 * 128 * 2 * 2.07e9
 # kernels grows in proportion to the matrices solved).
 CSRC = os.path.join(ROOT, "paper_2601_17979_gb300", "csrc")
 KERNEL_SOURCES = {
-    "fused": ("gesvj_fused.cuh", "jacobi_common.cuh", "fused_f32.cuh", "scalar.cuh"),
-    "persistent": ("gesvj_fused.cuh", "jacobi_common.cuh", "fused_f32.cuh", "scalar.cuh"),
+    "fused": ("gesvj_fused.cuh", "jacobi_common.cuh", "fused_f32.cuh", "scalar.cuh", "tc_f32.cuh"),
+    "persistent": ("gesvj_fused.cuh", "jacobi_common.cuh", "fused_f32.cuh", "scalar.cuh", "tc_f32.cuh"),
 }
 TRAFFIC_PER_MATRIX = {
-    # FP64 128x64, gesvj_fused_kernel<double,16,2,128>: 2,000-matrix launch
-    ("fused", "tall128x64_f64", "1d5f949baa2b"): 141.6e3,
-    # FP32 uneven sizes, gesvj_persistent_kernel<float,16,2,128>: 1,000-matrix launch
-    ("persistent", "uneven_f32", "1d5f949baa2b"): 58.8e9 / 1000,
+    # 128x64, gesvj_fused_kernel<double|float,16,2,128>: 2,000-matrix launches
+    ("fused", "tall128x64_f64", "a34d3b2688bf"): (139549184 + 141490176) / 2000,
+    ("fused", "tall128x64_f32", "a34d3b2688bf"): (67632384 + 40839936) / 2000,
 }
 
 
@@ -599,7 +598,7 @@ def run_serving(args, rank, world, local):
     seconds = args.seconds or cfg["seconds"]
     pool = {}
     srv = bsvd.Server(int(args.arena_gb * 1e9), max_inflight=32, fp64_prec=args.fp64_prec,
-                      big_flags=args.big_flags, max_big_batch=args.max_big_batch)
+                      big_flags=args.big_flags, max_big_batch=args.max_big_batch, big_k_fp64=args.big_k_fp64)
     # warm-up: a short low-rate stream (first launches set kernel attributes)
     for _ in range(max(1, args.warmup)):
         serve_stream(srv, 500.0, 0.2, 30.0, 1000 + rank, pool)
@@ -631,6 +630,7 @@ def run_serving(args, rank, world, local):
                                    "Haar factors; inputs from a pool of 2 matrices per (bin, shape, type)",
                        "arena_gb": args.arena_gb, "max_inflight": 32, "jobs": "U, Sigma, V",
                        "big_flags": args.big_flags, "max_big_batch": args.max_big_batch or 8,
+                       "big_k_fp64": args.big_k_fp64 or 256,
                        "fp64_prec": args.fp64_prec + " (FP64 / complex128 requests above 256 columns)",
                        "results": "left in the arena and released on completion (not copied back)",
                        "l2": "inputs read once from page-locked host memory"},
@@ -1093,6 +1093,8 @@ def main():
     ap.add_argument("--arena-gb", type=float, default=40.0, help="serving: device-memory budget")
     ap.add_argument("--big-flags", type=int, default=0, help="serving: flags added to multi-kernel batches")
     ap.add_argument("--max-big-batch", type=int, default=0, help="serving: requests per multi-kernel batch")
+    ap.add_argument("--big-k-fp64", type=int, default=0,
+                    help="serving: columns above which FP64 requests take the multi-kernel path (0: 256)")
     ap.add_argument("--fp64-prec", default="mixed", choices=["native", "mixed"],
                     help="serving: precision path of large FP64 requests (FP64 accuracy either way)")
     ap.add_argument("--sweep-rates", type=float, nargs="*", default=[25, 50, 100, 200])
@@ -1227,7 +1229,8 @@ def main():
                  "sweeps_mean": float(sw32.mean()), "sweeps_max": int(sw32.max()),
                  "info_nonzero": int((info32 != 0).sum()),
                  "roofline": {"bound": "alu", "achieved": flops32 / t32 / 1e12, "peak": PEAK_FP32 / 1e12,
-                              "unit": "TFLOP/s", "frac": flops32 / t32 / PEAK_FP32}},
+                              "unit": "TFLOP/s", "frac": flops32 / t32 / PEAK_FP32,
+                              "traffic": measured_traffic("fused", "tall128x64_f32", B)}},
         "roofline": {"bound": "alu", "achieved": flops64 / t64 / 1e12, "peak": PEAK_FP64 / 1e12,
                      "unit": "TFLOP/s", "frac": flops64 / t64 / PEAK_FP64, "traffic": measured_traffic("fused", "tall128x64_f64", B),
                      "kernel": "gesvj_fused_kernel<double,16,2,128>",

@@ -393,7 +393,10 @@ typedef struct {
                            BSVD_PREC_MIXED (FP32 sweeps + FP64 polish, FP64 accuracy)      */
     int big_flags;      /* further bsvd_opts.flags bits for multi-kernel batches (which always
                            run with bits 4 and 11: a host-replayed one-sweep graph)        */
-    int reserved[2];    /* zero                                                                  */
+    int big_k_fp64;     /* big_k for FP64 / complex128 requests; 0 = big_k.  A persistent
+                           batch solves each matrix on one SM: a smaller limit spreads
+                           the medium FP64 requests over the GPU                           */
+    int reserved[1];    /* zero                                                                  */
 } bsvd_server_opts;
 
 double bsvd_server_clock(void);

@@ -61,7 +61,7 @@ class BsvdError(RuntimeError):
 class ServerOpts(ctypes.Structure):
     _fields_ = [("max_inflight", ctypes.c_int), ("max_batch", ctypes.c_int), ("big_k", ctypes.c_int),
                 ("max_big_batch", ctypes.c_int), ("fp64_prec", ctypes.c_int), ("big_flags", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("big_k_fp64", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class Opts(ctypes.Structure):
@@ -535,7 +535,8 @@ class Server:
     """
 
     def __init__(self, arena_bytes: int, *, max_inflight: int = 0, max_batch: int = 0, big_k: int = 0,
-                 max_big_batch: int = 0, fp64_prec="native", big_flags: int = 0, device=None):
+                 max_big_batch: int = 0, fp64_prec="native", big_flags: int = 0, big_k_fp64: int = 0,
+                 device=None):
         self.lib = load()
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.device = dev
@@ -545,6 +546,7 @@ class Server:
         o.max_big_batch = int(max_big_batch)
         o.fp64_prec = PRECS[fp64_prec] if isinstance(fp64_prec, str) else int(fp64_prec)
         o.big_flags = int(big_flags)
+        o.big_k_fp64 = int(big_k_fp64)
         srv = ctypes.c_void_p()
         with torch.cuda.device(dev):
             st = self.lib.bsvd_server_create(self.arena.data_ptr(), self.arena.numel(), ctypes.byref(o),

@@ -131,6 +131,7 @@ struct bsvd_server_s {
     char* arena_base = nullptr;
     Arena* arena = nullptr;
     int max_inflight = 32, max_batch = 4096, big_k = 256, max_big_batch = 8, fp64_prec = 0, big_flags = 0;
+    int big_k_fp64 = 256;
     // per slot two streams: high priority for persistent batches (small
     // requests), low priority for multi-kernel batches (large ones), so the
     // block scheduler starts a small request's CTAs before a large batch's
@@ -163,7 +164,7 @@ struct bsvd_server_s {
 namespace {
 
 Key key_of(const bsvd_server_s* s, const Request* r) {
-    const bool big = r->k > s->big_k;
+    const bool big = r->k > ((r->dtype == 'd' || r->dtype == 'z') ? s->big_k_fp64 : s->big_k);
     return Key(r->dtype, (r->wantU ? 1 : 0) | (r->wantV ? 2 : 0), big ? 16 : auto_nb(r->k), big ? 1 : 0,
                big ? r->m : 0, big ? r->n : 0);
 }
@@ -602,13 +603,14 @@ bsvd_status bsvd_server_create(void* d_arena, size_t arena_bytes, const bsvd_ser
     if (!opts) opts = &z;
     if (opts->max_inflight < 0 || opts->max_inflight > 64 || opts->max_batch < 0 || opts->big_k < 0 ||
         opts->max_big_batch < 0 || (opts->fp64_prec != BSVD_PREC_NATIVE && opts->fp64_prec != BSVD_PREC_MIXED) ||
-        opts->big_flags < 0 || opts->big_flags > 4095)
+        opts->big_flags < 0 || opts->big_flags > 4095 || opts->big_k_fp64 < 0)
         return BSVD_ERR_INVALID;
     bsvd_server_s* s = new (std::nothrow) bsvd_server_s();
     if (!s) return BSVD_ERR_NOMEM;
     s->max_inflight = opts->max_inflight ? opts->max_inflight : 32;
     s->max_batch = opts->max_batch ? opts->max_batch : 4096;
     s->big_k = opts->big_k ? opts->big_k : 256;
+    s->big_k_fp64 = opts->big_k_fp64 ? opts->big_k_fp64 : s->big_k;
     s->max_big_batch = opts->max_big_batch ? opts->max_big_batch : 8;
     s->fp64_prec = opts->fp64_prec;
     s->big_flags = opts->big_flags;
