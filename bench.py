@@ -55,11 +55,16 @@ CSRC = os.path.join(ROOT, "paper_2601_17979_gb300", "csrc")
 KERNEL_SOURCES = {
     "fused": ("gesvj_fused.cuh", "jacobi_common.cuh", "fused_f32.cuh", "scalar.cuh", "tc_f32.cuh"),
     "persistent": ("gesvj_fused.cuh", "jacobi_common.cuh", "fused_f32.cuh", "scalar.cuh", "tc_f32.cuh"),
+    "uneven": ("gesvj_fused.cuh", "jacobi_common.cuh", "fused_f32.cuh", "scalar.cuh", "tc_f32.cuh",
+               "tc_c64.cuh", "gesvj_blocked.cuh", "blocked_launch.cuh"),
 }
 TRAFFIC_PER_MATRIX = {
     # 128x64, gesvj_fused_kernel<double|float,16,2,128>: 2,000-matrix launches
     ("fused", "tall128x64_f64", "a34d3b2688bf"): (139549184 + 141490176) / 2000,
     ("fused", "tall128x64_f32", "a34d3b2688bf"): (67632384 + 40839936) / 2000,
+    # the whole uneven step (every kernel of both types), 2,000-matrix case:
+    # 651.7 GB over the warm-up and the timed step
+    ("uneven", "uneven", "5771bdbdc4e8"): 651.66e9 / 2 / 2000,
 }
 
 
@@ -439,9 +444,9 @@ def run_uneven(args, rank, world, local):
             "gflops": flops / (ms * 1e-3) / 1e9,
             "roofline": {"bound": "alu", "achieved": flops / (ms * 1e-3) / 1e12, "peak": PEAK_FP32 / 1e12,
                          "unit": "TFLOP/s", "frac": flops / (ms * 1e-3) / PEAK_FP32,
-                         "traffic": measured_traffic("persistent", "uneven_f32",
-                                                     sum(1 for x in mats if x.dtype == np.float32)),
-                         "traffic_note": "FP32 persistent launch only (ncu, scaled by matrix count)"},
+                         "traffic": measured_traffic("uneven", "uneven", B),
+                         "traffic_note": "every kernel of the step, DRAM read + write (ncu on a 2,000-matrix "
+                                         "case, scaled by matrix count)"},
             "clocks": sampler.summary()}
     # the same matrices with one launch per distinct shape (the pointer-array
     # form grouping by shape) -- the path the persistent launch replaces
