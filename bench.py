@@ -636,7 +636,8 @@ def run_serving(args, rank, world, local):
                        "arena_gb": args.arena_gb, "max_inflight": 32, "jobs": "U, Sigma, V",
                        "big_flags": args.big_flags, "max_big_batch": args.max_big_batch or 8,
                        "big_k_fp64": args.big_k_fp64 or 256,
-                       "fp64_prec": args.fp64_prec + " (FP64 / complex128 requests above 256 columns)",
+                       "fp64_prec": args.fp64_prec + " (FP64 / complex128 requests above "
+                                     f"{args.big_k_fp64 or 256} columns)",
                        "results": "left in the arena and released on completion (not copied back)",
                        "l2": "inputs read once from page-locked host memory"},
             "latency_ms": main["latency_ms"], "serving": main, "rate_sweep": sweep,
@@ -1001,13 +1002,16 @@ def run_square(args, rank, world, local):
     rows = []
     sampler = ClockSampler(gpu_uuid(torch, dev))
     sampler.__enter__()
-    for t, dt in (("d", torch.float64), ("s", torch.float32)):
+    for t, dt in (("d", torch.float64), ("s", torch.float32), ("z", torch.complex128), ("c", torch.complex64)):
         if t not in args.square_dtypes:
             continue
         for n in sizes:
             B = args.batch if args.batch != BATCH else {64: 2000, 128: 1000, 256: 200, 512: 50}.get(n, 32)
-            rng = synth.rng_for(synth.SEED_BASE + 7, n * 2 + (t == "s"))
-            A = torch.from_numpy(rng.uniform(0, 1, (B, n, n))).to(dt).to(dev).transpose(1, 2)
+            rng = synth.rng_for(synth.SEED_BASE + 7, n * 2 + "dszc".index(t) % 2 + 2 * (t in "zc"))
+            a = rng.uniform(0, 1, (B, n, n))
+            if t in "zc":
+                a = a + 1j * rng.uniform(0, 1, (B, n, n))
+            A = torch.from_numpy(a).to(dt).to(dev).transpose(1, 2)
             holder = {}
 
             def call(A=A, holder=holder):
@@ -1017,20 +1021,23 @@ def run_square(args, rank, world, local):
             ms = statistics.median(times)
             sw = res.sweeps.cpu().numpy()
             nb = 16 if n >= 48 else (8 if n >= 12 else 4)
-            f = matrix_flops(n, n, nb, sw)
+            f = matrix_flops(n, n, nb, sw) * (4 if t in "zc" else 1)     # a complex MAC: four real ones
             rows.append({"dtype": t, "n": n, "batch": B, "ms": ms, "matrices_per_s": B / (ms * 1e-3),
                          "tflops": f / (ms * 1e-3) / 1e12, "sweeps_mean": float(sw.mean()),
                          "info_nonzero": int((res.info != 0).sum().item())})
             print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
     sampler.__exit__(None, None, None)
-    head = max(rows, key=lambda r: (r["dtype"] == "d", r["n"]))
-    peak_head = PEAK_FP64 if head["dtype"] == "d" else PEAK_FP32
+    head = max(rows, key=lambda r: (r["dtype"] == "d", r["dtype"] == "s", r["dtype"] == "z", r["n"]))
+    peak_head = PEAK_FP64 if head["dtype"] in "dz" else PEAK_FP32
+    tname = {"d": "FP64", "s": "FP32", "z": "complex128", "c": "complex64"}
     line = {"metric": f"batch SVD matrices/s (square {head['n']}x{head['n']} "
-                      f"{'FP64' if head['dtype'] == 'd' else 'FP32'}, U[0,1])",
+                      f"{tname[head['dtype']]}, U[0,1])",
             "value": head["matrices_per_s"], "unit": "matrices/s", "n_gpus": world, "steps": args.steps,
             "warmup": 1, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if head["dtype"] == "d" else "f32", "data": "synthetic",
-            "config": {"workload": "square: n x n, entries U[0,1], FP64 and FP32, U, Sigma, V; median of steps",
+            "vs_baseline": None, "dtype": {"d": "f64", "s": "f32", "z": "c128", "c": "c64"}[head["dtype"]],
+            "data": "synthetic",
+            "config": {"workload": "square: n x n, entries U[0,1] (complex: U[0,1] + i U[0,1]), "
+                                   f"types {args.square_dtypes}, U, Sigma, V; median of steps",
                        "flags": args.square_flags,
                        "l2": "L2 flushed (256 MB write) before every timed call"},
             "roofline": {"bound": "alu", "achieved": head["tflops"], "peak": peak_head / 1e12,
@@ -1038,8 +1045,8 @@ def run_square(args, rank, world, local):
                          "kernel": f"{head['dtype'].upper()} solve at n = {head['n']} (multi-kernel path above "
                                    "~100 columns)",
                          "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"},
-            "roofline_fp32": [{"n": r["n"], "achieved": r["tflops"], "peak": PEAK_FP32 / 1e12,
-                               "frac": r["tflops"] * 1e12 / PEAK_FP32} for r in rows if r["dtype"] == "s"],
+            "roofline_fp32": [{"dtype": r["dtype"], "n": r["n"], "achieved": r["tflops"], "peak": PEAK_FP32 / 1e12,
+                               "frac": r["tflops"] * 1e12 / PEAK_FP32} for r in rows if r["dtype"] in "sc"],
             "clocks": sampler.summary(), "results": rows}
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
@@ -1091,15 +1098,15 @@ def main():
                          "U[0,1] batches, n = 64..512")
     ap.add_argument("--sizes", type=int, nargs="*", default=None, help="square: the sizes n")
     ap.add_argument("--square-flags", type=int, default=0, help="square: bsvd_opts.flags of every solve")
-    ap.add_argument("--square-dtypes", default="ds", help="square: types to run, of 'd' and 's'")
+    ap.add_argument("--square-dtypes", default="ds", help="square: types to run, of 'd', 's', 'z' and 'c'")
     ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (default 50,000)")
     ap.add_argument("--seconds", type=float, default=0.0, help="serving: stream length (default 10 s)")
     ap.add_argument("--drain", type=float, default=10.0, help="serving: seconds to drain after arrivals")
     ap.add_argument("--arena-gb", type=float, default=40.0, help="serving: device-memory budget")
     ap.add_argument("--big-flags", type=int, default=0, help="serving: flags added to multi-kernel batches")
     ap.add_argument("--max-big-batch", type=int, default=0, help="serving: requests per multi-kernel batch")
-    ap.add_argument("--big-k-fp64", type=int, default=0,
-                    help="serving: columns above which FP64 requests take the multi-kernel path (0: 256)")
+    ap.add_argument("--big-k-fp64", type=int, default=128,
+                    help="serving: columns above which FP64 requests take the multi-kernel path (0: big_k, 256)")
     ap.add_argument("--fp64-prec", default="mixed", choices=["native", "mixed"],
                     help="serving: precision path of large FP64 requests (FP64 accuracy either way)")
     ap.add_argument("--sweep-rates", type=float, nargs="*", default=[25, 50, 100, 200])

@@ -15,9 +15,9 @@ from .binding import (BsvdError, SVDResult, Server, gesvj, gesvj_host, host_work
                       autotune, autotune_batched, persistent_plan, load, handle, make_opts,
                       column_major, empty_column_major, workspace_bytes, EXPORTS,
                       FLAG_NO_V_CORRECTION, FLAG_TWO_STAGE, FLAG_NO_MASKS, FLAG_NO_GRAPH,
-                      FLAG_SYNC_CHECK, FLAG_QR, FLAG_SPLIT_LARGE, FLAG_F32_FFMA, FLAG_WIDE_ANGLES, FLAG_NO_ONCHIP, FLAG_SPLIT_F32, FLAG_HOST_LOOP)
+                      FLAG_SYNC_CHECK, FLAG_QR, FLAG_SPLIT_LARGE, FLAG_F32_FFMA, FLAG_WIDE_ANGLES, FLAG_NO_ONCHIP, FLAG_SPLIT_F32, FLAG_HOST_LOOP, FLAG_THREE_KERNELS)
 
 __all__ = ["build", "BsvdError", "SVDResult", "Server", "gesvj", "gesvj_host", "host_workspace_bytes", "gesvj_batched", "autotune", "autotune_batched", "persistent_plan", "load", "handle",
            "make_opts", "column_major", "empty_column_major", "workspace_bytes", "EXPORTS",
            "FLAG_NO_V_CORRECTION", "FLAG_TWO_STAGE", "FLAG_NO_MASKS", "FLAG_NO_GRAPH",
-           "FLAG_SYNC_CHECK", "FLAG_QR", "FLAG_SPLIT_LARGE", "FLAG_F32_FFMA", "FLAG_WIDE_ANGLES", "FLAG_NO_ONCHIP", "FLAG_SPLIT_F32", "FLAG_HOST_LOOP"]
+           "FLAG_SYNC_CHECK", "FLAG_QR", "FLAG_SPLIT_LARGE", "FLAG_F32_FFMA", "FLAG_WIDE_ANGLES", "FLAG_NO_ONCHIP", "FLAG_SPLIT_F32", "FLAG_HOST_LOOP", "FLAG_THREE_KERNELS"]

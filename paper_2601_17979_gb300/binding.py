@@ -27,6 +27,7 @@ PATH_NAMES = {v: k for k, v in PATHS.items()}
 FLAG_NO_V_CORRECTION, FLAG_TWO_STAGE, FLAG_NO_MASKS, FLAG_NO_GRAPH, FLAG_SYNC_CHECK, FLAG_QR = 1, 2, 4, 8, 16, 32
 FLAG_SPLIT_LARGE = 64
 FLAG_F32_FFMA, FLAG_WIDE_ANGLES, FLAG_NO_ONCHIP, FLAG_SPLIT_F32, FLAG_HOST_LOOP = 128, 256, 512, 1024, 2048
+FLAG_THREE_KERNELS = 4096
 DTYPES = {torch.float32: "s", torch.float64: "d", torch.complex64: "c", torch.complex128: "z"}
 REAL = {torch.float32: torch.float32, torch.float64: torch.float64,
         torch.complex64: torch.float32, torch.complex128: torch.float64}

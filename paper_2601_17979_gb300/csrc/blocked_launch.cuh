@@ -8,6 +8,7 @@
 
 #include "blocked_layout.h"
 #include "gesvj_blocked.cuh"
+#include "gesvj_pairstep.cuh"
 #include "launch_util.cuh"
 #include "internal.h"
 
@@ -136,6 +137,12 @@ cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stag
         (e = allow_dynamic_smem<blk_update_stage1<T, NB>>()) != cudaSuccess ||
         (e = allow_dynamic_smem<blk_update_stage2<T, NB>>()) != cudaSuccess)
         return e;
+    // complex64, nb = 8 or 16, tensor cores: one pair-step kernel per round
+    // (flags bit 12: the three kernels)
+    constexpr bool kPairCapable = std::is_same<T, float2>::value && (NB == 8 || NB == 16);
+    const bool pairstep = kPairCapable && !two_stage && !(a.flags & (128 | 4096));
+    if constexpr (kPairCapable)
+        if (pairstep && (e = allow_dynamic_smem<blk_pairstep_c64<NB>>()) != cudaSuccess) return e;
 
     blk_load<T><<<a.count, kBlkThreads, 0, st>>>(a);
     const dim3 gpair(a.count, a.L / 2);
@@ -154,6 +161,11 @@ cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stag
     // one sweep: every round's stages, then the end-of-sweep bookkeeping
     auto sweep = [&](cudaStream_t s) -> cudaError_t {
         for (int r = 0; r < a.L - 1; ++r) {
+            if constexpr (kPairCapable)
+                if (pairstep) {
+                    blk_pairstep_c64<NB><<<gpair, kPairThreads, PairLayout<NB>::kBytes, s>>>(a, r);
+                    continue;
+                }
             // real FP32: the tensor cores (flags bit 7: FMA register tiles)
             if constexpr (std::is_same<T, float>::value && (NB == 8 || NB == 16)) {
                 if (a.flags & 128) blk_gram_f32<NB><<<gpair, kBlkThreads, 0, s>>>(a, r);

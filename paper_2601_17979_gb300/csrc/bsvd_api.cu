@@ -109,7 +109,7 @@ bool resolve(const bsvd_opts* o, bool single, int N, Resolved& r) {
     std::memset(&z, 0, sizeof z);
     if (!o) o = &z;
     if (o->nb < 0 || o->max_sweeps < 0 || o->inner_sweeps < 0 || o->tol < 0 || o->path < 0 ||
-        o->path > BSVD_PATH_PERSISTENT || o->flags < 0 || o->flags > 4095 || o->prec < 0 ||
+        o->path > BSVD_PATH_PERSISTENT || o->flags < 0 || o->flags > 8191 || o->prec < 0 ||
         o->prec > BSVD_PREC_MIXED || (o->prec == BSVD_PREC_MIXED && single))
         return false;
     r.nb = o->nb ? o->nb : (N >= 48 ? 16 : (N >= 12 ? 8 : 4));
@@ -275,7 +275,7 @@ bsvd_status plan_mixed(int max_smem, char t, int m, int n, int batch, bool wantU
     mp.r32.path = BSVD_PATH_AUTO;
     // FP32 sweeps: FMA tiles / FP64 rotations, and how the sweep loop runs
     // (no graph, host checks, host-replayed graph), as the caller asked
-    mp.r32.flags = r.flags & (128 | 256 | 8 | 16 | 2048);
+    mp.r32.flags = r.flags & (128 | 256 | 8 | 16 | 2048 | 4096);
     mp.r32.inner_sweeps = 1;
     mp.r32.prec = BSVD_PREC_NATIVE;
     mp.r64 = r;

@@ -603,7 +603,7 @@ bsvd_status bsvd_server_create(void* d_arena, size_t arena_bytes, const bsvd_ser
     if (!opts) opts = &z;
     if (opts->max_inflight < 0 || opts->max_inflight > 64 || opts->max_batch < 0 || opts->big_k < 0 ||
         opts->max_big_batch < 0 || (opts->fp64_prec != BSVD_PREC_NATIVE && opts->fp64_prec != BSVD_PREC_MIXED) ||
-        opts->big_flags < 0 || opts->big_flags > 4095 || opts->big_k_fp64 < 0)
+        opts->big_flags < 0 || opts->big_flags > 8191 || opts->big_k_fp64 < 0)
         return BSVD_ERR_INVALID;
     bsvd_server_s* s = new (std::nothrow) bsvd_server_s();
     if (!s) return BSVD_ERR_NOMEM;
