@@ -244,12 +244,26 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
     constexpr int NBLK = NB * (NB + 1) / 2, NBU = (NBLK + GT - 1) / GT;
     // J-update workers: every warp but the first when there is more than one
     constexpr int JW0 = GT > 32 ? 32 : 0, JWN = GT - JW0;
+    // The 2x2 blocks of G by slot pair: the NB (NB - 1) / 2 off-diagonal
+    // ones (two rotations each) first, then the NB diagonal ones (a closed
+    // form); a thread's items alternate in direction over the threads, so
+    // the blocks beyond the first GT go to the threads that hold diagonal
+    // ones, not to warp 0, which forms the next step's rotations.  Blocks
+    // are disjoint: the assignment does not change any result.
+    constexpr int NOFF = NB * (NB - 1) / 2;
     int bq1[NBU], bq2[NBU];
 #pragma unroll
     for (int u = 0; u < NBU; ++u) {
-        const int e = gt + u * GT;
-        if (e < NBLK) tri_index(e, bq1[u], bq2[u]);
-        else { bq1[u] = -1; bq2[u] = -1; }
+        const int e = u * GT + ((u & 1) ? GT - 1 - gt : gt);
+        if (e < NOFF) {
+            int a, c;
+            tri_index(e, a, c);           // a <= c: the strict pair (a, c + 1)
+            bq1[u] = a; bq2[u] = c + 1;
+        } else if (e < NBLK) {
+            bq1[u] = bq2[u] = e - NOFF;
+        } else {
+            bq1[u] = -1; bq2[u] = -1;
+        }
     }
     for (int e = gt; e < TWO * TWO; e += GT)
         J[(e % TWO) + (e / TWO) * LDG] = make_s<T>((e % TWO) == (e / TWO) ? 1 : 0);
