@@ -24,6 +24,24 @@ __device__ __forceinline__ void rr_pair(int L, int r, int q, int& i, int& j) {
     j = max(a, b);
 }
 
+// One slot's pair over consecutive round-robin steps: the ring positions of
+// its two players move back one place per step, so advancing costs two
+// compares instead of rr_pair's modular arithmetic.  Starts at step 0.
+struct RRSlot {
+    int L, slot, pa, pb;
+    __device__ __forceinline__ RRSlot(int L_, int slot_)
+        : L(L_), slot(slot_), pa(slot_ == 0 ? 0 : slot_ - 1), pb(L_ - 2 - slot_) {}
+    __device__ __forceinline__ void next() {
+        pa = pa == 0 ? L - 2 : pa - 1;
+        pb = pb == 0 ? L - 2 : pb - 1;
+    }
+    __device__ __forceinline__ void pair(int& i, int& j) const {
+        const int a = slot == 0 ? 0 : rr_start(L, pa), b = rr_start(L, pb);
+        i = min(a, b);
+        j = max(a, b);
+    }
+};
+
 // e -> (a, b), a <= b, for the column-major upper triangle
 __device__ __forceinline__ void tri_index(int e, int& a, int& b) {
     int c = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
@@ -124,10 +142,11 @@ __device__ __forceinline__ double2 rot_sub(double2 x, double c, double2 y, doubl
                         fma(-y.x, e.y, fma(-y.y, e.x, __dmul_rn(x.y, c))));
 }
 
-// t = sign(x) y / (|x| + hypot(x, y)), y > 0.  FP32: sqrt and a fast division
-// (a couple of ulp) within the range where x^2 + y^2 neither overflows nor
-// underflows -- any t close to the exact one gives an orthogonal rotation,
-// since c = 1/sqrt(1 + t^2) and s = t c.  FP64: IEEE hypot and division.
+// t = sign(x) y / (|x| + hypot(x, y)), y > 0.  Within the range where
+// x^2 + y^2 neither overflows nor underflows the hypotenuse is one square
+// root of an FMA (hypot elsewhere); FP32 then divides with the fast division
+// (a couple of ulp), FP64 with the IEEE one.  Any t close to the exact one
+// gives an orthogonal rotation, since c = 1/sqrt(1 + t^2) and s = t c.
 __device__ __forceinline__ float rotation_tan(float x, float y) {
     const float ax = fabsf(x), m = fmaxf(ax, y);
     const float h = (m > 1e-18f && m < 1e18f) ? sqrtf(fmaf(x, x, __fmul_rn(y, y))) : hypotf(x, y);
@@ -135,7 +154,22 @@ __device__ __forceinline__ float rotation_tan(float x, float y) {
     return (m > 1e-18f && m < 1e18f) ? __fdividef(yy, ax + h) : yy / (ax + h);
 }
 __device__ __forceinline__ double rotation_tan(double x, double y) {
-    return (x >= 0 ? y : -y) / (fabs(x) + hypot(x, y));
+    const double ax = fabs(x), m = fmax(ax, y);
+    const double h = (m > 1e-150 && m < 1e150) ? sqrt(fma(x, x, __dmul_rn(y, y))) : hypot(x, y);
+    return (x >= 0 ? y : -y) / (ax + h);
+}
+
+// |g_pq| for the pair test and the rotation: the same one-square-root form
+// for complex entries in the safe range, hypot elsewhere.
+__device__ __forceinline__ float abs_rot(float x) { return fabsf(x); }
+__device__ __forceinline__ double abs_rot(double x) { return fabs(x); }
+__device__ __forceinline__ float abs_rot(float2 z) {
+    const float m = fmaxf(fabsf(z.x), fabsf(z.y));
+    return (m > 1e-18f && m < 1e18f) ? sqrtf(fmaf(z.x, z.x, __fmul_rn(z.y, z.y))) : hypotf(z.x, z.y);
+}
+__device__ __forceinline__ double abs_rot(double2 z) {
+    const double m = fmax(fabs(z.x), fabs(z.y));
+    return (m > 1e-150 && m < 1e150) ? sqrt(fma(z.x, z.x, __dmul_rn(z.y, z.y))) : hypot(z.x, z.y);
 }
 
 // FP64 counterparts of the single-precision types, for rotations computed in
@@ -160,7 +194,7 @@ __device__ __forceinline__ int inner_rotation_wide(const T* G, Real<T> tol, int 
     constexpr int LDG = 2 * NB + 1;
     const RW gpp = (RW)re(G[p + p * LDG]), gqq = (RW)re(G[q + q * LDG]);
     const TW gpq = to_wide(G[p + q * LDG]);
-    const RW apq = abs_s(gpq), tw = (RW)tol;
+    const RW apq = abs_rot(gpq), tw = (RW)tol;
     // squares of widened single-precision values stay inside FP64's range
     const bool fire = gpp > 0 && gqq > 0 && apq > 0 && apq * apq >= (tw * tw) * (gpp * gqq);
     RW c = 1, t = 0;
@@ -177,28 +211,28 @@ __device__ __forceinline__ int inner_rotation_wide(const T* G, Real<T> tol, int 
     return fire;
 }
 
-// One thread's rotation for slot `slot` of round-robin step `st` on the 2NB
-// indices: test |g_pq| >= tol sqrt(g_pp) sqrt(g_qq) (Alg. 1) and form
-// (c, s, e^{i phi}) by Eq. (sin-cos) with sign(0) = +1.  Returns fired.
-// `wide` (single precision only): test and rotation in FP64.
+// One thread's rotation for slot `slot` (index pair p < q of the current
+// round-robin step on the 2NB indices): test |g_pq| >= tol sqrt(g_pp)
+// sqrt(g_qq) (Alg. 1) and form (c, s, e^{i phi}) by Eq. (sin-cos) with
+// sign(0) = +1.  Returns fired.  `wide` (single precision only): test and
+// rotation in FP64.
 template <class T, int NB>
-__device__ __forceinline__ int inner_rotation(const T* G, Real<T> tol, int st, int slot,
+__device__ __forceinline__ int inner_rotation(const T* G, Real<T> tol, int p, int q, int slot,
                                               typename InnerTables<T, NB>::Slot* out, bool wide = false) {
     using R = Real<T>;
     constexpr int TWO = 2 * NB, LDG = TWO + 1;
-    int p, q;
-    rr_pair(TWO, st, slot, p, q);
     if constexpr (!std::is_same<T, typename WideOf<T>::type>::value)
         if (wide) return inner_rotation_wide<T, NB>(G, tol, p, q, slot, out);
     const R gpp = re(G[p + p * LDG]), gqq = re(G[q + q * LDG]);
     const T gpq = G[p + q * LDG];
-    const R apq = abs_s(gpq);
+    const R apq = abs_rot(gpq);
     // |g_pq| >= tol sqrt(g_pp) sqrt(g_qq), compared in squares while the
-    // product stays well inside the normal range
+    // product stays well inside the normal range; evaluated without
+    // short-circuit branches (every operand is finite or the test is false)
     const R prod = rmul(gpp, gqq);
-    const bool fire = gpp > 0 && gqq > 0 && apq > 0 &&
-                      (prod > kJacobiProdMin<R> ? rmul(apq, apq) >= rmul(rmul(tol, tol), prod)
-                                                : apq >= rmul(rmul(tol, sqrt_r(gpp)), sqrt_r(gqq)));
+    const bool sq = rmul(apq, apq) >= rmul(rmul(tol, tol), prod);
+    const bool fire = (gpp > 0) & (gqq > 0) & (apq > 0) &
+                      (prod > kJacobiProdMin<R> ? sq : apq >= rmul(rmul(tol, sqrt_r(gpp)), sqrt_r(gqq)));
     R c = 1, t = 0;
     T es = make_s<T>(0);
     if (fire) {
@@ -269,8 +303,13 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
         J[(e % TWO) + (e / TWO) * LDG] = make_s<T>((e % TWO) == (e / TWO) ? 1 : 0);
     if (gt == 0) { tb.count[0] = 0; tb.count[1] = 0; }
     named_sync(bar, GT);
-    if (gt < 32) {   // warp 0 forms the rotations; one ballot counts the fired ones
-        const int f = gt < NB ? inner_rotation<T, NB>(G, tol, 0, gt, tb.step(0), wide) : 0;
+    // warp 0 forms the rotations, lane `slot` those of one slot, following
+    // its pair through the steps; one ballot counts the fired ones
+    RRSlot rs(TWO, gt < NB ? gt : 0);
+    if (gt < 32) {
+        int p = 0, q = 0;
+        rs.pair(p, q);
+        const int f = gt < NB ? inner_rotation<T, NB>(G, tol, p, q, gt, tb.step(0), wide) : 0;
         const unsigned m = __ballot_sync(0xffffffffu, f);
         if (gt == 0) tb.count[0] += __popc(m);
     }
@@ -309,7 +348,7 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
                     if (!f1[u] && !f2[u]) continue;
                     if (bq1[u] == bq2[u]) {
                         // diagonal block: closed form, off-diagonal set to zero
-                        const R apq = abs_s(b01[u]);
+                        const R apq = abs_rot(b01[u]);
                         b00[u] = make_s<T>(fma_s(t1[u], apq, re(b00[u])));
                         b11[u] = make_s<T>(fma_s(-t1[u], apq, re(b11[u])));
                         b01[u] = make_s<T>(0);
@@ -350,7 +389,10 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
             const bool last = (st + 1 == STEPS);
             if (gt < 32 && !(last && isw + 1 == sweeps)) {
                 const int nisw = last ? isw + 1 : isw;
-                const int f = gt < NB ? inner_rotation<T, NB>(G, tol, last ? 0 : st + 1, gt, tb.step((gs + 1) & 1), wide) : 0;
+                int p = 0, q = 0;
+                rs.next();                    // step st + 1, or step 0 of the next sweep (2NB - 1 = 0 mod the ring)
+                rs.pair(p, q);
+                const int f = gt < NB ? inner_rotation<T, NB>(G, tol, p, q, gt, tb.step((gs + 1) & 1), wide) : 0;
                 const unsigned m = __ballot_sync(0xffffffffu, f);
                 if (gt == 0) tb.count[nisw & 1] += __popc(m);
             }
