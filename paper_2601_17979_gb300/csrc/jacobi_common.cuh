@@ -172,6 +172,59 @@ __device__ __forceinline__ double abs_rot(double2 z) {
     return (m > 1e-150 && m < 1e150) ? sqrt(fma(z.x, z.x, __dmul_rn(z.y, z.y))) : hypot(z.x, z.y);
 }
 
+// Bit patterns ordered like the values for non-negative reals (and below
+// zero for negative ones): sign and range tests on the integer pipes, which
+// the FP64 pipe does not share.
+__device__ __forceinline__ int as_ord(float x) { return __float_as_int(x); }
+__device__ __forceinline__ long long as_ord(double x) { return __double_as_longlong(x); }
+template <class R> struct RotRange;
+template <> struct RotRange<float> { static constexpr float lo = 1e-18f, hi = 1e18f; };
+template <> struct RotRange<double> { static constexpr double lo = 1e-150, hi = 1e150; };
+
+// Eq. (sin-cos) for x = g_pp - g_qq and y = 2|g_pq| > 0.  With h = hypot(x, y)
+// and d = |x| + h:  t = sign(x) y / d,  c = 1/sqrt(1 + t^2) = d / sqrt(d^2 + y^2),
+// and since d^2 + y^2 = 2 h d:  c = d r,  s = t c = sign(x) y r,  t = s (2 h r),
+// with r = 1/sqrt(2 h d) and h = q/sqrt(q), q = x^2 + y^2 -- two reciprocal
+// square roots and no division.  Used where q and 2 h d neither overflow nor
+// underflow (max(|x|, y) in [lo, hi]); elsewhere t = sign(x) y / (|x| + h),
+// c = 1/sqrt(1 + t^2), s = t c.  sign(0) = +1 (x = g_pp - g_qq is never -0).
+template <class R>
+__device__ __forceinline__ void rotation_cst(R x, R y, R& c, R& s, R& t) {
+    const R ax = abs_s(x);
+    const auto bm = as_ord(ax) > as_ord(y) ? as_ord(ax) : as_ord(y);
+    if (bm > as_ord(RotRange<R>::lo) && bm < as_ord(RotRange<R>::hi)) {
+        const R q = fma_s(x, x, rmul(y, y));
+        const R h = rmul(q, rsqrt_r(q));
+        const R d = ax + h, h2 = h + h;
+        const R r = rsqrt_r(rmul(h2, d));
+        const R sy = rmul(y, r);
+        s = as_ord(x) >= 0 ? sy : -sy;
+        c = rmul(d, r);
+        t = rmul(s, rmul(h2, r));
+    } else {
+        t = rotation_tan(x, y);
+        c = rsqrt_r(fma_s(t, t, R(1)));
+        s = rmul(t, c);
+    }
+}
+
+// e^{i phi} s for the rotation, phi the phase of g_pq (|g_pq| = a > 0):
+// for real data the sign of g_pq applied to s.
+__device__ __forceinline__ float phase_times(float g, float, float s) {
+    return __int_as_float(__float_as_int(s) ^ (__float_as_int(g) & (int)0x80000000u));
+}
+__device__ __forceinline__ double phase_times(double g, double, double s) {
+    return __longlong_as_double(__double_as_longlong(s) ^ (__double_as_longlong(g) & (long long)0x8000000000000000ull));
+}
+__device__ __forceinline__ float2 phase_times(float2 g, float a, float s) {
+    const float k = s * (1.0f / a);
+    return make_float2(g.x * k, g.y * k);
+}
+__device__ __forceinline__ double2 phase_times(double2 g, double a, double s) {
+    const double k = s * (1.0 / a);
+    return make_double2(g.x * k, g.y * k);
+}
+
 // FP64 counterparts of the single-precision types, for rotations computed in
 // FP64 from FP32 Gram entries (the mixed-precision option).
 template <class T> struct WideOf { using type = T; };
@@ -200,9 +253,9 @@ __device__ __forceinline__ int inner_rotation_wide(const T* G, Real<T> tol, int 
     RW c = 1, t = 0;
     TW es = make_s<TW>(0);
     if (fire) {
-        t = rotation_tan(gpp - gqq, 2 * apq);
-        c = 1.0 / sqrt(fma(t, t, 1.0));
-        es = scale(phase_s(gpq, apq), t * c);
+        RW sn;
+        rotation_cst(gpp - gqq, 2 * apq, c, sn, t);
+        es = phase_times(gpq, apq, sn);
     }
     typename InnerTables<T, NB>::Slot rec;
     rec.c = (R)c; rec.t = (R)t; rec.es = to_narrow(es);
@@ -227,21 +280,21 @@ __device__ __forceinline__ int inner_rotation(const T* G, Real<T> tol, int p, in
     const T gpq = G[p + q * LDG];
     const R apq = abs_rot(gpq);
     // |g_pq| >= tol sqrt(g_pp) sqrt(g_qq), compared in squares while the
-    // product stays well inside the normal range; evaluated without
-    // short-circuit branches (every operand is finite or the test is false)
+    // product stays well inside the normal range; the sign and range tests
+    // on the bit patterns (a NaN operand still fails the comparison)
     const R prod = rmul(gpp, gqq);
-    const bool sq = rmul(apq, apq) >= rmul(rmul(tol, tol), prod);
-    const bool fire = (gpp > 0) & (gqq > 0) & (apq > 0) &
-                      (prod > kJacobiProdMin<R> ? sq : apq >= rmul(rmul(tol, sqrt_r(gpp)), sqrt_r(gqq)));
+    const bool pos = (as_ord(gpp) > 0) & (as_ord(gqq) > 0) & (as_ord(apq) > 0);
+    const bool fire = pos && (as_ord(prod) > as_ord(kJacobiProdMin<R>)
+                                  ? rmul(apq, apq) >= rmul(rmul(tol, tol), prod)
+                                  : apq >= rmul(rmul(tol, sqrt_r(gpp)), sqrt_r(gqq)));
     R c = 1, t = 0;
     T es = make_s<T>(0);
     if (fire) {
         // tau = x / y with x = g_pp - g_qq, y = 2 |g_pq|:
         // t = sign(tau) / (|tau| + sqrt(1 + tau^2)) = sign(x) y / (|x| + hypot(x, y))
-        const R x = gpp - gqq, y = 2 * apq;
-        t = rotation_tan(x, y);
-        c = rsqrt_r(fma_s(t, t, R(1)));
-        es = scale(phase_s(gpq, apq), t * c);
+        R sn;
+        rotation_cst(gpp - gqq, 2 * apq, c, sn, t);
+        es = phase_times(gpq, apq, sn);
     }
     typename InnerTables<T, NB>::Slot rec;
     rec.c = c; rec.t = t; rec.es = es;
