@@ -354,17 +354,18 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
     }
     for (int e = gt; e < TWO * TWO; e += GT)
         J[(e % TWO) + (e / TWO) * LDG] = make_s<T>((e % TWO) == (e / TWO) ? 1 : 0);
-    if (gt == 0) { tb.count[0] = 0; tb.count[1] = 0; }
     named_sync(bar, GT);
     // warp 0 forms the rotations, lane `slot` those of one slot, following
-    // its pair through the steps; one ballot counts the fired ones
+    // its pair through the steps (the next step's pair is found during the
+    // block transforms, where warp 0 is not the last to finish); one ballot
+    // counts the fired ones, summed per sweep in a register of thread 0 and
+    // stored to tb.count[sweep parity] at the sweep's last step
     RRSlot rs(TWO, gt < NB ? gt : 0);
+    int np = 0, nq = 0, fired_sweep = 0;
     if (gt < 32) {
-        int p = 0, q = 0;
-        rs.pair(p, q);
-        const int f = gt < NB ? inner_rotation<T, NB>(G, tol, p, q, gt, tb.step(0), wide) : 0;
-        const unsigned m = __ballot_sync(0xffffffffu, f);
-        if (gt == 0) tb.count[0] += __popc(m);
+        rs.pair(np, nq);
+        const int f = gt < NB ? inner_rotation<T, NB>(G, tol, np, nq, gt, tb.step(0), wide) : 0;
+        fired_sweep = __popc(__ballot_sync(0xffffffffu, f));
     }
     named_sync(bar, GT);
     int seen = 0;
@@ -436,22 +437,32 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
                     }
                 }
             }
+            if (gt < 32) {
+                rs.next();                    // step st + 1, or step 0 of the next sweep (2NB - 1 = 0 mod the ring)
+                rs.pair(np, nq);
+            }
             named_sync(bar, GT);
             // warp 0: the rotations of the next step (this sweep, or the first
             // step of the next one) from the updated G
             const bool last = (st + 1 == STEPS);
-            if (gt < 32 && !(last && isw + 1 == sweeps)) {
-                const int nisw = last ? isw + 1 : isw;
-                int p = 0, q = 0;
-                rs.next();                    // step st + 1, or step 0 of the next sweep (2NB - 1 = 0 mod the ring)
-                rs.pair(p, q);
-                const int f = gt < NB ? inner_rotation<T, NB>(G, tol, p, q, gt, tb.step((gs + 1) & 1), wide) : 0;
-                const unsigned m = __ballot_sync(0xffffffffu, f);
-                if (gt == 0) tb.count[nisw & 1] += __popc(m);
-            }
+            auto form_next = [&]() {
+                unsigned m = 0;
+                if (!(last && isw + 1 == sweeps)) {
+                    const int f = gt < NB ? inner_rotation<T, NB>(G, tol, np, nq, gt, tb.step((gs + 1) & 1), wide) : 0;
+                    m = __ballot_sync(0xffffffffu, f);
+                }
+                if (gt == 0) {
+                    if (last) {       // sweep isw complete; m starts sweep isw + 1
+                        tb.count[isw & 1] = fired_sweep;
+                        fired_sweep = __popc(m);
+                    } else {
+                        fired_sweep += __popc(m);
+                    }
+                }
+            };
             // the other warps: J <- J R for every rotating slot of this step
             // (items are disjoint: all loads, then the math, then the stores)
-            if (gt >= JW0) {
+            auto update_j = [&]() {
                 constexpr int NJU = (TWO * NB + JWN - 1) / JWN;
                 int fj[NJU], pj[NJU], qj[NJU], ij[NJU];
                 R cj[NJU];
@@ -477,13 +488,21 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
                         J[ij[u] + qj[u] * LDG] = rot_sub(yj[u], cj[u], xj[u], es);
                     }
                 bg(gs * inner_background_warps<GT>() + (gt - JW0) / 32);
+            };
+            if constexpr (JW0 == 0) {          // one warp: both, in turn
+                form_next();
+                update_j();
+            } else if (gt < 32) {
+                form_next();
+            } else {
+                update_j();
             }
             named_sync(bar, GT);
             if (nsteps) *nsteps = gs + 1;
         }
+        // written by thread 0 before the last barrier; rewritten only at the
+        // end of sweep isw + 2, after every thread has passed this point
         const int fired = tb.count[isw & 1];
-        named_sync(bar, GT);           // all have read it before it is reset
-        if (gt == 0) tb.count[isw & 1] = 0;   // reused by sweep isw + 2
         seen += fired;
         if (fired == 0) break;         // a sweep with no rotation: the inner solve has converged
     }
