@@ -235,11 +235,24 @@ __device__ __forceinline__ double2 to_wide(float2 x) { return make_double2((doub
 __device__ __forceinline__ float to_narrow(double x) { return __double2float_rn(x); }
 __device__ __forceinline__ float2 to_narrow(double2 x) { return make_float2(__double2float_rn(x.x), __double2float_rn(x.y)); }
 
+// The pair's diagonal 2 x 2 block of G <- R^H G R by the closed form:
+// g_pp += t |g_pq|, g_qq -= t |g_pq|, g_pq = g_qp = 0.  Applied by the lane
+// that formed the rotation, as soon as it is formed: in the steps between,
+// no other block transform and no other lane reads these four entries.
+template <class T, int LDG>
+__device__ __forceinline__ void diagonal_block(T* G, int p, int q, Real<T> gpp, Real<T> gqq, Real<T> apq,
+                                               Real<T> t) {
+    G[p + p * LDG] = make_s<T>(fma_s(t, apq, gpp));
+    G[q + q * LDG] = make_s<T>(fma_s(-t, apq, gqq));
+    G[p + q * LDG] = make_s<T>(0);
+    G[q + p * LDG] = make_s<T>(0);
+}
+
 // The rotation of inner_rotation with the pair test and Eq. (sin-cos)
 // evaluated in FP64 on the single-precision Gram entries (exactly widened),
 // c, t and e s rounded once to the working precision at the end.
 template <class T, int NB>
-__device__ __forceinline__ int inner_rotation_wide(const T* G, Real<T> tol, int p, int q, int slot,
+__device__ __forceinline__ int inner_rotation_wide(T* G, Real<T> tol, int p, int q, int slot,
                                                    typename InnerTables<T, NB>::Slot* out) {
     using R = Real<T>;
     using TW = typename WideOf<T>::type;
@@ -261,6 +274,8 @@ __device__ __forceinline__ int inner_rotation_wide(const T* G, Real<T> tol, int 
     rec.c = (R)c; rec.t = (R)t; rec.es = to_narrow(es);
     rec.pqf = p | (q << 8) | ((fire ? 1 : 0) << 16);
     out[slot] = rec;
+    // the closed form in the working precision, with the rounded t
+    if (fire) diagonal_block<T, LDG>(G, p, q, (R)gpp, (R)gqq, abs_rot(G[p + q * LDG]), rec.t);
     return fire;
 }
 
@@ -270,7 +285,7 @@ __device__ __forceinline__ int inner_rotation_wide(const T* G, Real<T> tol, int 
 // sign(0) = +1.  Returns fired.  `wide` (single precision only): test and
 // rotation in FP64.
 template <class T, int NB>
-__device__ __forceinline__ int inner_rotation(const T* G, Real<T> tol, int p, int q, int slot,
+__device__ __forceinline__ int inner_rotation(T* G, Real<T> tol, int p, int q, int slot,
                                               typename InnerTables<T, NB>::Slot* out, bool wide = false) {
     using R = Real<T>;
     constexpr int TWO = 2 * NB, LDG = TWO + 1;
@@ -300,6 +315,7 @@ __device__ __forceinline__ int inner_rotation(const T* G, Real<T> tol, int p, in
     rec.c = c; rec.t = t; rec.es = es;
     rec.pqf = p | (q << 8) | ((fire ? 1 : 0) << 16);
     out[slot] = rec;
+    if (fire) diagonal_block<T, LDG>(G, p, q, gpp, gqq, apq, t);
     return fire;
 }
 
@@ -328,26 +344,25 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
                             int gt, int bar, const Bg& bg = Bg(), int* nsteps = nullptr, bool wide = false) {
     using R = Real<T>;
     constexpr int TWO = 2 * NB, LDG = TWO + 1, STEPS = TWO - 1;
-    constexpr int NBLK = NB * (NB + 1) / 2, NBU = (NBLK + GT - 1) / GT;
+    // The off-diagonal 2x2 blocks of G by slot pair (two rotations each);
+    // the diagonal ones (the closed form) are applied by the lane of warp 0
+    // that forms their rotation, right after forming it.
+    constexpr int NOFF = NB * (NB - 1) / 2, NBU = (NOFF + GT - 1) / GT;
     // J-update workers: every warp but the first when there is more than one
     constexpr int JW0 = GT > 32 ? 32 : 0, JWN = GT - JW0;
-    // The 2x2 blocks of G by slot pair: the NB (NB - 1) / 2 off-diagonal
-    // ones (two rotations each) first, then the NB diagonal ones (a closed
-    // form); a thread's items alternate in direction over the threads, so
-    // the blocks beyond the first GT go to the threads that hold diagonal
-    // ones, not to warp 0, which forms the next step's rotations.  Blocks
-    // are disjoint: the assignment does not change any result.
-    constexpr int NOFF = NB * (NB - 1) / 2;
+    // Items of the first round go to the last NOFF threads (at most warp 0's
+    // 32 threads left idle, so that warp 0 can find the next step's pairs
+    // meanwhile); further rounds alternate in direction.  Blocks are
+    // disjoint: the assignment does not change any result.
+    constexpr int BASE = GT - NOFF < 0 ? 0 : (GT - NOFF < 32 ? GT - NOFF : 32);
     int bq1[NBU], bq2[NBU];
 #pragma unroll
     for (int u = 0; u < NBU; ++u) {
-        const int e = u * GT + ((u & 1) ? GT - 1 - gt : gt);
-        if (e < NOFF) {
+        const int e = u * GT + ((u & 1) ? GT - 1 - gt : gt - BASE);
+        if (e >= 0 && e < NOFF) {
             int a, c;
             tri_index(e, a, c);           // a <= c: the strict pair (a, c + 1)
             bq1[u] = a; bq2[u] = c + 1;
-        } else if (e < NBLK) {
-            bq1[u] = bq2[u] = e - NOFF;
         } else {
             bq1[u] = -1; bq2[u] = -1;
         }
@@ -378,7 +393,7 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
             // then the stores, so their latencies overlap.
             {
                 int f1[NBU], f2[NBU], p1[NBU], r1[NBU], p2[NBU], r2[NBU];
-                R c1[NBU], c2[NBU], t1[NBU];
+                R c1[NBU], c2[NBU];
                 T e1[NBU], e2[NBU], b00[NBU], b01[NBU], b10[NBU], b11[NBU];
 #pragma unroll
                 for (int u = 0; u < NBU; ++u) {
@@ -388,7 +403,7 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
                     f1[u] = s1.pqf >> 16; f2[u] = s2.pqf >> 16;
                     p1[u] = s1.pqf & 255; r1[u] = (s1.pqf >> 8) & 255;
                     p2[u] = s2.pqf & 255; r2[u] = (s2.pqf >> 8) & 255;
-                    c1[u] = s1.c; c2[u] = s2.c; t1[u] = s1.t;
+                    c1[u] = s1.c; c2[u] = s2.c;
                     e1[u] = s1.es; e2[u] = s2.es;
                 }
 #pragma unroll
@@ -400,15 +415,6 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
 #pragma unroll
                 for (int u = 0; u < NBU; ++u) {
                     if (!f1[u] && !f2[u]) continue;
-                    if (bq1[u] == bq2[u]) {
-                        // diagonal block: closed form, off-diagonal set to zero
-                        const R apq = abs_rot(b01[u]);
-                        b00[u] = make_s<T>(fma_s(t1[u], apq, re(b00[u])));
-                        b11[u] = make_s<T>(fma_s(-t1[u], apq, re(b11[u])));
-                        b01[u] = make_s<T>(0);
-                        b10[u] = make_s<T>(0);
-                        continue;
-                    }
                     if (f2[u]) {   // columns (p2, r2) times R2
                         const T es = e2[u], ces = conj_s(es);
                         const T n00 = rot_add(b00[u], c2[u], b01[u], ces);
@@ -431,10 +437,8 @@ __device__ int inner_jacobi(T* G, T* J, const InnerTables<T, NB>& tb, Real<T> to
                     if (!f1[u] && !f2[u]) continue;
                     G[p1[u] + p2[u] * LDG] = b00[u]; G[p1[u] + r2[u] * LDG] = b01[u];
                     G[r1[u] + p2[u] * LDG] = b10[u]; G[r1[u] + r2[u] * LDG] = b11[u];
-                    if (bq1[u] != bq2[u]) {
-                        G[p2[u] + p1[u] * LDG] = conj_s(b00[u]); G[r2[u] + p1[u] * LDG] = conj_s(b01[u]);
-                        G[p2[u] + r1[u] * LDG] = conj_s(b10[u]); G[r2[u] + r1[u] * LDG] = conj_s(b11[u]);
-                    }
+                    G[p2[u] + p1[u] * LDG] = conj_s(b00[u]); G[r2[u] + p1[u] * LDG] = conj_s(b01[u]);
+                    G[p2[u] + r1[u] * LDG] = conj_s(b10[u]); G[r2[u] + r1[u] * LDG] = conj_s(b11[u]);
                 }
             }
             if (gt < 32) {
