@@ -31,13 +31,25 @@ namespace bsvd {
 constexpr int kPairThreads = 128;
 constexpr int kPairVirtualWarps = kBlkThreads / 32;    // the Gram kernel's warps
 
-// Shared memory: the staged 64-row panel chunk and the virtual warps'
+// 8-byte global -> shared copies that do not wait for the data (the next
+// panel chunk loads while the tensor cores work on the current one); a
+// source size of 0 writes zeros.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Shared memory: two staged 64-row panel chunks and the virtual warps'
 // partial blocks (S2), reused for J's split fragments (S4/S5); then G and J
 // (leading dimension 2nb + 1) and the rotation tables.
 template <int NB>
 struct PairLayout {
     static constexpr int TWO = 2 * NB, LDG = TWO + 1, KP = kGramChunk + 4;
-    static constexpr int kStage = (KP * TWO * (int)sizeof(float2) + 15) & ~15;
+    static constexpr int kChunk = (KP * TWO * (int)sizeof(float2) + 15) & ~15;
+    static constexpr int kStage = 2 * kChunk;
     static constexpr int kRed = kPairVirtualWarps * 32 * 16 * (int)sizeof(float);
     static constexpr int kFrag = jc_fragment_bytes<NB>();
     static constexpr int kRegionA = ((kStage + kRed > kFrag ? kStage + kRed : kFrag) + 15) & ~15;
@@ -79,18 +91,32 @@ __global__ void __launch_bounds__(kPairThreads, 3) blk_pairstep_c64(const Blocke
             for (int j = 0; j < 2; ++j)
 #pragma unroll
                 for (int i = 0; i < 4; ++i) re[h][j][i] = im[h][j][i] = 0.f;
-        for (int k0 = 0; k0 < M; k0 += KC) {
+        // chunk k0 of the pair's columns into buffer `buf` (rows past M as zeros)
+        auto stage = [&](int buf, int k0) {
             const int kc = min(KC, M - k0);
+            float2* Pb = P + buf * (L::kChunk / (int)sizeof(float2));
             for (int e = tid; e < KC * TWO; e += NT) {
                 const int kk = e % KC, c = e / KC;
                 const int col = c < NB ? bi * NB + c : bj * NB + (c - NB);
-                P[kk + c * KP] = kk < kc ? Wm[k0 + kk + (long long)col * M] : make_float2(0.f, 0.f);
+                cp_async8(Pb + kk + c * KP, Wm + k0 + (kk < kc ? kk : 0) + (long long)col * M, kk < kc ? 8 : 0);
+            }
+            cp_async_commit();
+        };
+        stage(0, 0);
+        for (int k0 = 0, it = 0; k0 < M; k0 += KC, ++it) {
+            const int kc = min(KC, M - k0);
+            if (k0 + KC < M) {                 // the next chunk loads during this one
+                stage((it + 1) & 1, k0 + KC);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
             }
             __syncthreads();
+            const float2* Pc = P + (it & 1) * (L::kChunk / (int)sizeof(float2));
 #pragma unroll
             for (int h = 0; h < H; ++h)
-                gram_c64_block_acc<NB>(P, KP, kc, 0, NB, bm, bn, (warp + h * NW) / NB2, WPB, lane, re[h], im[h]);
-            __syncthreads();
+                gram_c64_block_acc<NB>(Pc, KP, kc, 0, NB, bm, bn, (warp + h * NW) / NB2, WPB, lane, re[h], im[h]);
+            __syncthreads();                   // before this buffer is refilled
         }
 #pragma unroll
         for (int h = 0; h < H; ++h)
