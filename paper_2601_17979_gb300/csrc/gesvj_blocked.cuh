@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kBlkThreads) blk_gram_f32_tc(const BlockedArgs
     constexpr int WPB = NW / NB2;                       // warps per block
     static_assert(NW % NB2 == 0, "warps per Gram block");
     constexpr int KC = kGramChunk, KP = KC + 4;
-    __shared__ __align__(16) float P[KP * TWO];
+    __shared__ __align__(16) float P[2][KP * TWO];     // two chunks: the next loads during this one
     __shared__ float red[NW * 32 * 8];
     const int b = blockIdx.x, q = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (blk_skip(a, b)) return;
@@ -157,16 +157,27 @@ __global__ void __launch_bounds__(kBlkThreads) blk_gram_f32_tc(const BlockedArgs
     for (int j = 0; j < 2; ++j)
 #pragma unroll
         for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
-    for (int k0 = 0; k0 < M; k0 += KC) {
+    auto stage = [&](int buf, int k0) {        // zero tail: adds nothing
         const int kc = min(KC, M - k0);
         for (int e = tid; e < KC * TWO; e += NT) {
             const int kk = e % KC, c = e / KC;
             const int col = c < NB ? bi * NB + c : bj * NB + (c - NB);
-            P[kk + c * KP] = kk < kc ? W[k0 + kk + (long long)col * M] : 0.f;   // zero tail: adds nothing
+            cp_async<4>(&P[buf][kk + c * KP], W + k0 + (kk < kc ? kk : 0) + (long long)col * M, kk < kc ? 4 : 0);
+        }
+        cp_async_commit();
+    };
+    stage(0, 0);
+    for (int k0 = 0, it = 0; k0 < M; k0 += KC, ++it) {
+        const int kc = min(KC, M - k0);
+        if (k0 + KC < M) {
+            stage((it + 1) & 1, k0 + KC);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
-        gram_block_acc<NB>(P, KP, kc, 0, NB, bm, bn, sub, WPB, lane, acc);
-        __syncthreads();
+        gram_block_acc<NB>(P[it & 1], KP, kc, 0, NB, bm, bn, sub, WPB, lane, acc);
+        __syncthreads();                        // before this buffer is refilled
     }
 #pragma unroll
     for (int j = 0; j < 2; ++j)

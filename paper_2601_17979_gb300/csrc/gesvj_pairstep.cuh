@@ -31,17 +31,6 @@ namespace bsvd {
 constexpr int kPairThreads = 128;
 constexpr int kPairVirtualWarps = kBlkThreads / 32;    // the Gram kernel's warps
 
-// 8-byte global -> shared copies that do not wait for the data (the next
-// panel chunk loads while the tensor cores work on the current one); a
-// source size of 0 writes zeros.
-__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
 // Shared memory: two staged 64-row panel chunks and the virtual warps'
 // partial blocks (S2), reused for J's split fragments (S4/S5); then G and J
 // (leading dimension 2nb + 1) and the rotation tables.
@@ -98,7 +87,7 @@ __global__ void __launch_bounds__(kPairThreads, 3) blk_pairstep_c64(const Blocke
             for (int e = tid; e < KC * TWO; e += NT) {
                 const int kk = e % KC, c = e / KC;
                 const int col = c < NB ? bi * NB + c : bj * NB + (c - NB);
-                cp_async8(Pb + kk + c * KP, Wm + k0 + (kk < kc ? kk : 0) + (long long)col * M, kk < kc ? 8 : 0);
+                cp_async<8>(Pb + kk + c * KP, Wm + k0 + (kk < kc ? kk : 0) + (long long)col * M, kk < kc ? 8 : 0);
             }
             cp_async_commit();
         };
