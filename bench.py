@@ -307,24 +307,25 @@ def run_reference_square32(args, world):
     print(json.dumps(line), flush=True)
 
 
-# matrices with min(m, n) >= 128 run as one variable-shape multi-kernel
-# batch per type beside the persistent launches (flags bit 6, and bit 10 for
-# real FP32; measured 3.53 s against 3.68 s per step with FP32 kept
-# persistent); bit 4 is the host-checked stop, used only where graphs are off
+# matrices with min(m, n) >= 128 (complex64) or 160 (FP32) run as one
+# variable-shape multi-kernel batch per type beside the persistent launches
+# (flags bit 6, and bit 10 for real FP32; measured 3.53 s against 3.68 s per
+# step with FP32 kept persistent); bit 4 is the host-checked stop, used only
+# where graphs are off
 UNEVEN_FLAGS = 64 | 16 | 1024
-SPLIT_K = 128
 
 
-def uneven_launches(groups, res, plans, steps, nb=16):
+def uneven_launches(groups, res, plans, steps, flags, nb=16):
     """Kernel launches of one uneven step: one persistent launch per segment
-    of each type, and for the complex64 split the multi-kernel batch's load,
-    sweeps (each L_max - 1 rounds of Gram, eigensolver and update, then the
-    convergence and loop-control kernels; the device stops the loop once all
-    have converged) and three finalisation kernels."""
+    of each type, and for each split batch the multi-kernel batch's load,
+    sweeps (each L_max - 1 rounds -- one pair-step kernel for complex64, the
+    Gram, eigensolver and update kernels for FP32 or with flags bit 7 or 12
+    -- then the convergence and loop-control kernels; the device stops the
+    loop once all have converged) and three finalisation kernels."""
     n = sum(plans[dt][2] for dt in res)
     for dt, r in res.items():
-        if not np.issubdtype(dt, np.complexfloating):
-            continue
+        cplx = np.issubdtype(dt, np.complexfloating)
+        per_round = 1 if cplx and not (flags & (128 | 4096)) else 3
         sw = r.sweeps.cpu().numpy()
         big = [(x.shape, k) for x, k, w in zip(groups[dt], sw, plans[dt][1]) if w == 2]
         if not big:
@@ -332,7 +333,7 @@ def uneven_launches(groups, res, plans, steps, nb=16):
         l = max(-(-min(s) // nb) for s, _ in big)
         L = l + (l & 1)
         issued = int(max(k for _, k in big))
-        n += 1 + issued * (3 * (L - 1) + 2) + 3
+        n += 1 + issued * (per_round * (L - 1) + 2) + 3
     return n * steps
 
 
@@ -431,10 +432,11 @@ def run_uneven(args, rank, world, local):
                        "matrices_per_rank": B, "flags": args.uneven_flags,
                        "path": "persistent launches per type (one per block width x shared memory / global "
                                "slot segment, block width per size bucket, autotuned), one stream per type; "
-                               "matrices with k >= 128 as one variable-shape multi-kernel batch per type "
+                               "matrices with k >= 128 (complex64) or 160 (FP32) as one variable-shape "
+                               "multi-kernel batch per type "
                                "beside them",
                        "l2": "inputs larger than L2"},
-            "gpu_launches": uneven_launches(groups, res, plans, args.steps), "info_nonzero": int((info != 0).sum()),
+            "gpu_launches": uneven_launches(groups, res, plans, args.steps, args.uneven_flags), "info_nonzero": int((info != 0).sum()),
             "segments": buckets,
             "autotune": ({"seconds": tune_s, "sample_per_bucket": args.tune_sample,
                           "buckets": {k: [[b["M"], b["N"], b["nb"]] + [round(b["ms"][w], 3) for w in (4, 8, 16)]
@@ -1114,7 +1116,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="mixed96: skip the optional mixed variants")
     ap.add_argument("--uneven-flags", type=int, default=UNEVEN_FLAGS,
-                    help="uneven: bsvd_opts.flags of the persistent calls (default: split complex64 k >= 128)")
+                    help="uneven: bsvd_opts.flags of the persistent calls (default: split complex64 k >= 128, FP32 k >= 160)")
     ap.add_argument("--no-autotune", action="store_true", help="uneven: skip the per-bucket autotuning")
     ap.add_argument("--tune-sample", type=int, default=64, help="uneven: autotuning sample per bucket")
     ap.add_argument("--no-per-shape", action="store_true",

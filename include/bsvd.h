@@ -138,7 +138,8 @@ typedef struct {
                           rounded once to FP32;
                           bit 9: BSVD_PATH_PERSISTENT keeps every matrix in a global
                           workspace slot (no shared-memory segments);
-                          bit 10: with bit 6, real FP32 batches split the same way;
+                          bit 10: with bit 6, real FP32 batches split the same way,
+                          from min(m, n) >= 160;
                           bit 11: the masked multi-kernel path replays a one-sweep
                           graph from the host (bit 4 applies) instead of the
                           device-side conditional loop;

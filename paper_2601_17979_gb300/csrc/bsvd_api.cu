@@ -839,7 +839,7 @@ bsvd_status persistent_impl(bsvd_handle h, char t, const TypeOps& ops, bool want
 }
 
 // ---- flags bit 6: split an uneven complex64 persistent batch ------------------
-// Matrices with min(m, n) >= kSplitK run on the multi-kernel path as one
+// Matrices with min(m, n) >= split_k run on the multi-kernel path as one
 // variable-shape batch (per-matrix shapes, CUDA-graph sweeps) on a stream of
 // the handle, beside the persistent launch for the rest.  With W in global
 // memory the persistent kernel's inner solver runs four block pairs per SM;
@@ -850,8 +850,12 @@ bsvd_status persistent_impl(bsvd_handle h, char t, const TypeOps& ops, bool want
 // variable-shape batch was slower (1.31 s against 1.20 s), so the flag
 // leaves other types in the persistent launch.
 // Flags bit 10 extends the split to real FP32 (measured on the uneven
-// workload; the default leaves FP32 in the persistent launches).
-constexpr int kFlagSplit = 64, kFlagSplitF32 = 1024, kSplitK = 128;
+// workload; the default leaves FP32 in the persistent launches), from
+// min(m, n) >= 160: batches of 600 matrices m ~ U{n..2n} took 23.7 ms in the
+// persistent launch against 27.1 split at n = 128, 31.3 against 32.4 at 144,
+// 39.4 against 37.5 at 160 (complex64 at n = 128: 41.8 against 36.0).
+constexpr int kFlagSplit = 64, kFlagSplitF32 = 1024;
+int split_k(const TypeOps& ops) { return ops.elt == 8 ? 128 : 160; }
 
 bool split_large(const TypeOps& ops, const bsvd_opts* opts) {
     if (!ops.single || !opts || opts->path != BSVD_PATH_PERSISTENT || !(opts->flags & kFlagSplit)) return false;
@@ -870,8 +874,9 @@ void plan_split(const TypeOps& ops, int batch, const int* m, const int* n, const
     sp.excl.assign(batch, 0);
     sp.ids.clear();
     std::vector<int> mm, nn;
+    const int k_split = split_k(ops);
     for (int i = 0; i < batch; ++i)
-        if (std::min(m[i], n[i]) >= kSplitK) {
+        if (std::min(m[i], n[i]) >= k_split) {
             sp.excl[i] = 1;
             sp.ids.push_back(i);
             mm.push_back(m[i]);
