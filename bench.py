@@ -1008,7 +1008,9 @@ def run_square(args, rank, world, local):
         if t not in args.square_dtypes:
             continue
         for n in sizes:
-            B = args.batch if args.batch != BATCH else {64: 2000, 128: 1000, 256: 200, 512: 50}.get(n, 32)
+            # the paper's square benchmark: batches of 1,000 matrices (FP64 and
+            # complex128 n = 512: 200, to keep a run within minutes)
+            B = args.batch if args.batch != BATCH else (200 if t in "dz" and n >= 512 else 1000)
             rng = synth.rng_for(synth.SEED_BASE + 7, n * 2 + "dszc".index(t) % 2 + 2 * (t in "zc"))
             a = rng.uniform(0, 1, (B, n, n))
             if t in "zc":
@@ -1039,7 +1041,8 @@ def run_square(args, rank, world, local):
             "vs_baseline": None, "dtype": {"d": "f64", "s": "f32", "z": "c128", "c": "c64"}[head["dtype"]],
             "data": "synthetic",
             "config": {"workload": "square: n x n, entries U[0,1] (complex: U[0,1] + i U[0,1]), "
-                                   f"types {args.square_dtypes}, U, Sigma, V; median of steps",
+                                   f"types {args.square_dtypes}, U, Sigma, V; batches of 1,000 matrices "
+                                   "(FP64 / complex128 n = 512: 200) unless --batch; median of steps",
                        "flags": args.square_flags,
                        "l2": "L2 flushed (256 MB write) before every timed call"},
             "roofline": {"bound": "alu", "achieved": head["tflops"], "peak": peak_head / 1e12,
@@ -1100,7 +1103,7 @@ def main():
                          "U[0,1] batches, n = 64..512")
     ap.add_argument("--sizes", type=int, nargs="*", default=None, help="square: the sizes n")
     ap.add_argument("--square-flags", type=int, default=0, help="square: bsvd_opts.flags of every solve")
-    ap.add_argument("--square-dtypes", default="ds", help="square: types to run, of 'd', 's', 'z' and 'c'")
+    ap.add_argument("--square-dtypes", default="dsc", help="square: types to run, of 'd', 's', 'z' and 'c'")
     ap.add_argument("--rate", type=float, default=0.0, help="serving: arrivals per second (default 50,000)")
     ap.add_argument("--seconds", type=float, default=0.0, help="serving: stream length (default 10 s)")
     ap.add_argument("--drain", type=float, default=10.0, help="serving: seconds to drain after arrivals")
