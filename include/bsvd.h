@@ -143,10 +143,10 @@ typedef struct {
                           bit 11: the masked multi-kernel path replays a one-sweep
                           graph from the host (bit 4 applies) instead of the
                           device-side conditional loop;
-                          bit 12: complex64 with nb = 8 or 16 on the multi-kernel
-                          path runs each round as three kernels (Gram, eigensolver,
-                          update, G and J through global memory) instead of one
-                          pair-step kernel (same results)                            */
+                          bit 12: single precision (FP32, complex64) with nb = 8 or
+                          16 on the multi-kernel path runs each round as three
+                          kernels (Gram, eigensolver, update, G and J through global
+                          memory) instead of one pair-step kernel (same results)      */
     int prec;          /* bsvd_prec; MIXED only for d/z.  Pointer-array batches run MIXED per
                           shape group (also with BSVD_PATH_PERSISTENT), reading A and
                           writing S, U, V through the pointer arrays                     */

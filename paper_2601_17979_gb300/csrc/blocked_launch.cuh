@@ -137,12 +137,12 @@ cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stag
         (e = allow_dynamic_smem<blk_update_stage1<T, NB>>()) != cudaSuccess ||
         (e = allow_dynamic_smem<blk_update_stage2<T, NB>>()) != cudaSuccess)
         return e;
-    // complex64, nb = 8 or 16, tensor cores: one pair-step kernel per round
-    // (flags bit 12: the three kernels)
-    constexpr bool kPairCapable = std::is_same<T, float2>::value && (NB == 8 || NB == 16);
+    // single precision, nb = 8 or 16, tensor cores: one pair-step kernel per
+    // round (flags bit 12: the three kernels)
+    constexpr bool kPairCapable = (std::is_same<T, float>::value || std::is_same<T, float2>::value) && (NB == 8 || NB == 16);
     const bool pairstep = kPairCapable && !two_stage && !(a.flags & (128 | 4096));
     if constexpr (kPairCapable)
-        if (pairstep && (e = allow_dynamic_smem<blk_pairstep_c64<NB>>()) != cudaSuccess) return e;
+        if (pairstep && (e = allow_dynamic_smem<blk_pairstep<T, NB>>()) != cudaSuccess) return e;
 
     blk_load<T><<<a.count, kBlkThreads, 0, st>>>(a);
     const dim3 gpair(a.count, a.L / 2);
@@ -163,7 +163,7 @@ cudaError_t blk_run_nb(BlockedArgs a, void* work, cudaStream_t st, bool two_stag
         for (int r = 0; r < a.L - 1; ++r) {
             if constexpr (kPairCapable)
                 if (pairstep) {
-                    blk_pairstep_c64<NB><<<gpair, kPairThreads, PairLayout<NB>::kBytes, s>>>(a, r);
+                    blk_pairstep<T, NB><<<gpair, kPairThreads, PairLayout<T, NB>::kBytes, s>>>(a, r);
                     continue;
                 }
             // real FP32: the tensor cores (flags bit 7: FMA register tiles)

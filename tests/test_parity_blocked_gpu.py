@@ -173,7 +173,7 @@ def test_host_convergence_check_gives_same_bits(dtype):
     assert np.array_equal(S1, S2) and np.array_equal(U1, U2) and np.array_equal(V1, V2)
 
 
-@pytest.mark.parametrize("flags", [0, bsvd.FLAG_F32_FFMA, bsvd.FLAG_WIDE_ANGLES])
+@pytest.mark.parametrize("flags", [0, bsvd.FLAG_F32_FFMA, bsvd.FLAG_WIDE_ANGLES, bsvd.FLAG_THREE_KERNELS])
 @pytest.mark.parametrize("m,n,nb", [(200, 150, 16), (257, 33, 8), (150, 260, 16)])
 def test_blocked_fp32_tensor_core_and_ffma(flags, m, n, nb):
     """The multi-kernel FP32 Gram and update on the tensor cores (default),
@@ -199,13 +199,17 @@ def test_blocked_complex64_tensor_core_and_ffma(flags, m, n, nb):
     check(mats, S, U, V, info, ref["S"], f"c64 flags {flags} {m}x{n}")
 
 
+@pytest.mark.parametrize("dtype", [np.complex64, np.float32])
 @pytest.mark.parametrize("m,n,nb,extra", [(200, 150, 16, 0), (257, 33, 8, 0), (150, 260, 16, 0), (70, 200, 8, 0),
                                           (333, 97, 16, bsvd.FLAG_WIDE_ANGLES), (96, 96, 8, bsvd.FLAG_NO_MASKS)])
-def test_pairstep_equals_three_kernels_bitwise(m, n, nb, extra):
-    """The complex64 pair-step kernel performs each stage's operations in the
-    order of the three per-round kernels (flags bit 12): the same bits."""
+def test_pairstep_equals_three_kernels_bitwise(dtype, m, n, nb, extra):
+    """The pair-step kernel performs each stage's operations in the order of
+    the three per-round kernels (flags bit 12): the same bits."""
     rng = np.random.default_rng(m + 7 * n + nb + extra)
-    mats = [(rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))).astype(np.complex64) for _ in range(4)]
+    if dtype == np.complex64:
+        mats = [(rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))).astype(dtype) for _ in range(4)]
+    else:
+        mats = [rng.standard_normal((m, n)).astype(dtype) for _ in range(4)]
     S1, U1, V1, i1, w1 = run_gpu(mats, nb=nb, path="blocked", flags=extra)
     S2, U2, V2, i2, w2 = run_gpu(mats, nb=nb, path="blocked", flags=extra | bsvd.FLAG_THREE_KERNELS)
     assert (i1 == 0).all() and (i2 == 0).all() and np.array_equal(w1, w2)
