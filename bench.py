@@ -318,14 +318,13 @@ UNEVEN_FLAGS = 64 | 16 | 1024
 def uneven_launches(groups, res, plans, steps, flags, nb=16):
     """Kernel launches of one uneven step: one persistent launch per segment
     of each type, and for each split batch the multi-kernel batch's load,
-    sweeps (each L_max - 1 rounds -- one pair-step kernel for complex64, the
-    Gram, eigensolver and update kernels for FP32 or with flags bit 7 or 12
-    -- then the convergence and loop-control kernels; the device stops the
-    loop once all have converged) and three finalisation kernels."""
+    sweeps (each L_max - 1 rounds -- one pair-step kernel, or the Gram,
+    eigensolver and update kernels with flags bit 7 or 12 -- then the
+    convergence and loop-control kernels; the device stops the loop once all
+    have converged) and three finalisation kernels."""
     n = sum(plans[dt][2] for dt in res)
+    per_round = 3 if flags & (128 | 4096) else 1
     for dt, r in res.items():
-        cplx = np.issubdtype(dt, np.complexfloating)
-        per_round = 1 if cplx and not (flags & (128 | 4096)) else 3
         sw = r.sweeps.cpu().numpy()
         big = [(x.shape, k) for x, k, w in zip(groups[dt], sw, plans[dt][1]) if w == 2]
         if not big:

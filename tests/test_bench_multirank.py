@@ -70,8 +70,7 @@ def test_uneven_launch_count():
     each type (from the plan), and for each split batch (the plan's
     where = 2) the multi-kernel batch's load, max-sweeps sweeps of
     k (L_max - 1) + 2 kernels (the device stops the loop; k = 1 for the
-    complex64 pair step, 3 for FP32 or with flags bit 7 or 12) and three
-    finalisation kernels."""
+    pair step, 3 with flags bit 7 or 12) and three finalisation kernels."""
     from types import SimpleNamespace
     f32, c64 = np.dtype(np.float32), np.dtype(np.complex64)
     groups = {f32: [np.zeros((300, 200), np.float32), np.zeros((100, 90), np.float32)],
@@ -81,14 +80,13 @@ def test_uneven_launch_count():
            c64: SimpleNamespace(sweeps=torch.tensor([20, 13, 9]))}
     plans = {f32: (np.array([16, 16]), np.array([2, 0]), 1),
              c64: (np.array([8, 16, 16]), np.array([1, 2, 2]), 1)}
-    # FP32 split: n = 200 -> l = 13 blocks, L = 14; 12 sweeps issued, three kernels a round
-    # complex64 split: n up to 300 -> l = 19 blocks, L = 20; 13 sweeps issued, one kernel a round
-    f32_split = 1 + 12 * (3 * 13 + 2) + 3
-    per_step = 2 + f32_split + 1 + 13 * (1 * 19 + 2) + 3
+    # FP32 split: n = 200 -> l = 13 blocks, L = 14; 12 sweeps issued
+    # complex64 split: n up to 300 -> l = 19 blocks, L = 20; 13 sweeps issued
+    per_step = 2 + 1 + 12 * (1 * 13 + 2) + 3 + 1 + 13 * (1 * 19 + 2) + 3
     assert bench.uneven_launches(groups, res, plans, steps=1, flags=0) == per_step
     assert bench.uneven_launches(groups, res, plans, steps=3, flags=0) == 3 * per_step
-    # flags bit 12: complex64 rounds as three kernels
-    three = 2 + f32_split + 1 + 13 * (3 * 19 + 2) + 3
+    # flags bit 12: rounds as three kernels
+    three = 2 + 1 + 12 * (3 * 13 + 2) + 3 + 1 + 13 * (3 * 19 + 2) + 3
     assert bench.uneven_launches(groups, res, plans, steps=1, flags=4096) == three
     res_small = {f32: SimpleNamespace(sweeps=torch.tensor([12])), c64: SimpleNamespace(sweeps=torch.tensor([20]))}
     plans_small = {f32: (np.array([16]), np.array([0]), 1), c64: (np.array([8]), np.array([1]), 1)}
