@@ -307,7 +307,7 @@ def run_reference_square32(args, world):
     print(json.dumps(line), flush=True)
 
 
-# matrices with min(m, n) >= 128 (complex64) or 160 (FP32) run as one
+# matrices with min(m, n) >= 112 (complex64) or 144 (FP32) run as one
 # variable-shape multi-kernel batch per type beside the persistent launches
 # (flags bit 6, and bit 10 for real FP32; measured 3.53 s against 3.68 s per
 # step with FP32 kept persistent); bit 4 is the host-checked stop, used only
@@ -431,7 +431,7 @@ def run_uneven(args, rank, world, local):
                        "matrices_per_rank": B, "flags": args.uneven_flags,
                        "path": "persistent launches per type (one per block width x shared memory / global "
                                "slot segment, block width per size bucket, autotuned), one stream per type; "
-                               "matrices with k >= 128 (complex64) or 160 (FP32) as one variable-shape "
+                               "matrices with k >= 112 (complex64) or 144 (FP32) as one variable-shape "
                                "multi-kernel batch per type "
                                "beside them",
                        "l2": "inputs larger than L2"},
@@ -1118,7 +1118,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="mixed96: skip the optional mixed variants")
     ap.add_argument("--uneven-flags", type=int, default=UNEVEN_FLAGS,
-                    help="uneven: bsvd_opts.flags of the persistent calls (default: split complex64 k >= 128, FP32 k >= 160)")
+                    help="uneven: bsvd_opts.flags of the persistent calls (default: split complex64 k >= 112, FP32 k >= 144)")
     ap.add_argument("--no-autotune", action="store_true", help="uneven: skip the per-bucket autotuning")
     ap.add_argument("--tune-sample", type=int, default=64, help="uneven: autotuning sample per bucket")
     ap.add_argument("--no-per-shape", action="store_true",

@@ -121,7 +121,7 @@ typedef struct {
                           min(m, n)-square R by the path `path` selects, U = Q [U_R; 0].
                           Workspace: bsvd_gesvj_workspace with the same options;
                           bit 6: with BSVD_PATH_PERSISTENT on a complex64 pointer-array
-                          batch, the matrices with min(m, n) >= 128 run as one
+                          batch, the matrices with min(m, n) >= 112 run as one
                           variable-shape batch on the masked multi-kernel path (same
                           per-matrix arithmetic as that path on each shape alone), on a
                           stream the handle owns that is forked from and joined back to
@@ -139,7 +139,7 @@ typedef struct {
                           bit 9: BSVD_PATH_PERSISTENT keeps every matrix in a global
                           workspace slot (no shared-memory segments);
                           bit 10: with bit 6, real FP32 batches split the same way,
-                          from min(m, n) >= 160;
+                          from min(m, n) >= 144;
                           bit 11: the masked multi-kernel path replays a one-sweep
                           graph from the host (bit 4 applies) instead of the
                           device-side conditional loop;

@@ -850,12 +850,13 @@ bsvd_status persistent_impl(bsvd_handle h, char t, const TypeOps& ops, bool want
 // variable-shape batch was slower (1.31 s against 1.20 s), so the flag
 // leaves other types in the persistent launch.
 // Flags bit 10 extends the split to real FP32 (measured on the uneven
-// workload; the default leaves FP32 in the persistent launches), from
-// min(m, n) >= 160: batches of 600 matrices m ~ U{n..2n} took 23.7 ms in the
-// persistent launch against 27.1 split at n = 128, 31.3 against 32.4 at 144,
-// 39.4 against 37.5 at 160 (complex64 at n = 128: 41.8 against 36.0).
+// workload; the default leaves FP32 in the persistent launches).  The split
+// starts at min(m, n) >= 112 for complex64 and 144 for FP32: batches of 600
+// matrices m ~ U{n..2n} took (persistent launch against split, ms) complex64
+// 24.8 / 24.6 at n = 96, 33.9 / 29.3 at 112; FP32 21.3 / 22.9 at 112,
+// 23.7 / 25.4 at 128, 31.7 / 30.1 at 144.
 constexpr int kFlagSplit = 64, kFlagSplitF32 = 1024;
-int split_k(const TypeOps& ops) { return ops.elt == 8 ? 128 : 160; }
+int split_k(const TypeOps& ops) { return ops.elt == 8 ? 112 : 144; }
 
 bool split_large(const TypeOps& ops, const bsvd_opts* opts) {
     if (!ops.single || !opts || opts->path != BSVD_PATH_PERSISTENT || !(opts->flags & kFlagSplit)) return false;

@@ -99,14 +99,15 @@ def test_persistent_jobs_none():
 
 @pytest.mark.parametrize("dtype", [np.complex64, np.float32])
 def test_split_large_bitwise(dtype):
-    """Flags bit 6: complex64 matrices with min(m, n) >= 128 run as one
+    """Flags bit 6: complex64 matrices with min(m, n) >= 112 run as one
     variable-shape multi-kernel batch beside the persistent launch.  Each of
     them gets the bits of the multi-kernel path run on its shape alone (the
     kernels do the same per-matrix arithmetic; rounds and pairs a smaller
     matrix lacks are skipped), each of the rest the bits of the plain
     persistent launch.  FP32 batches ignore the flag."""
     rng = np.random.default_rng(31)
-    shapes = [(300, 150), (40, 30), (128, 128), (140, 260), (64, 20), (513, 129), (90, 90), (0, 4), (200, 131)]
+    shapes = [(300, 150), (40, 30), (128, 128), (140, 260), (64, 20), (513, 129), (90, 90), (0, 4), (200, 131),
+              (120, 115), (111, 200)]
     cplx = np.issubdtype(dtype, np.complexfloating)
     mats = [(rng.uniform(-1, 1, s) + (1j * rng.uniform(-1, 1, s) if cplx else 0)).astype(dtype) for s in shapes]
     S, U, V, info, sw = run_batched(mats, path="persistent", flags=bsvd.FLAG_SPLIT_LARGE)
@@ -116,7 +117,7 @@ def test_split_large_bitwise(dtype):
     for k, (A, (m, n)) in enumerate(zip(mats, shapes)):
         if min(m, n) == 0:
             continue
-        if min(m, n) >= 128 and cplx:
+        if min(m, n) >= 112 and cplx:
             S1, U1, V1, i1, w1 = run_batched([A], path="blocked", nb=16)
         else:
             S1, U1, V1, i1, w1 = [Sp[k]], [Up[k]], [Vp[k]], [ip[k]], [wp[k]]
@@ -131,8 +132,8 @@ def test_split_large_uneven_sample_and_jobs(cplx):
     """The uneven workload's recipe with the split, parity with the oracle;
     then without U and V."""
     pool = [(i, synth.matrix("uneven", i)) for i in range(1 if cplx else 0, 160, 2)]
-    big = [x for _, x in pool if min(x.shape) >= 128][:4]
-    small = [x for _, x in pool if min(x.shape) < 128][:6]
+    big = [x for _, x in pool if min(x.shape) >= 112][:4]
+    small = [x for _, x in pool if min(x.shape) < 112][:6]
     mats = big + small
     S, U, V, info, sw = run_batched(mats, path="persistent", flags=bsvd.FLAG_SPLIT_LARGE | bsvd.FLAG_SYNC_CHECK)
     ref = oracle.gesvj(mats)
