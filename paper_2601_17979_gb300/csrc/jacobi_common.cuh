@@ -325,8 +325,9 @@ __device__ __forceinline__ int inner_rotation(T* G, Real<T> tol, int p, int q, i
 // ordering on the 2NB indices, each applying nb disjoint rotations:
 // G <- R^H G R as 2x2 block transforms (rows of one slot, columns of another;
 // the diagonal block by the closed form g_pp += t|g_pq|, g_qq -= t|g_pq|,
-// g_pq = 0) and J <- J R.  Pipelined: while the other warps apply step s to
-// J, warp 0 already forms the rotations of step s+1 from the updated G.
+// g_pq = 0, applied by the lane that forms the rotation) and J <- J R.
+// Pipelined: while the other warps apply step s to J, warp 0 already forms
+// the rotations of step s+1 from the updated G.
 // Sweeps stop early once one rotates nothing.  Executed by GT threads (index
 // gt) sharing named barrier `bar`; the caller must have finished writing G and
 // synchronised.  Returns the number of rotations fired (0: G was diagonal to
