@@ -56,15 +56,15 @@ KERNEL_SOURCES = {
     "fused": ("gesvj_fused.cuh", "jacobi_common.cuh", "fused_f32.cuh", "scalar.cuh", "tc_f32.cuh"),
     "persistent": ("gesvj_fused.cuh", "jacobi_common.cuh", "fused_f32.cuh", "scalar.cuh", "tc_f32.cuh"),
     "uneven": ("gesvj_fused.cuh", "jacobi_common.cuh", "fused_f32.cuh", "scalar.cuh", "tc_f32.cuh",
-               "tc_c64.cuh", "gesvj_blocked.cuh", "blocked_launch.cuh"),
+               "tc_c64.cuh", "gesvj_blocked.cuh", "blocked_launch.cuh", "gesvj_pairstep.cuh"),
 }
 TRAFFIC_PER_MATRIX = {
     # 128x64, gesvj_fused_kernel<double|float,16,2,128>: 2,000-matrix launches
-    ("fused", "tall128x64_f64", "a34d3b2688bf"): (139549184 + 141490176) / 2000,
-    ("fused", "tall128x64_f32", "a34d3b2688bf"): (67632384 + 40839936) / 2000,
+    ("fused", "tall128x64_f64", "1aaf66d2379b"): (137736960 + 143072256) / 2000,
+    ("fused", "tall128x64_f32", "1aaf66d2379b"): (65926400 + 40410624) / 2000,
     # the whole uneven step (every kernel of both types), 2,000-matrix case:
-    # 651.7 GB over the warm-up and the timed step
-    ("uneven", "uneven", "5771bdbdc4e8"): 651.66e9 / 2 / 2000,
+    # 497.7 GB over the warm-up and the timed step
+    ("uneven", "uneven", "fa908dd456c8"): 497.71e9 / 2 / 2000,
 }
 
 
