@@ -216,8 +216,8 @@ def test_persistent_plan_host_logic():
     (no GPU needed): the block width follows min(m, n) (>= 48: 16, >= 12: 8,
     else 4) unless opts.nb is given; small matrices keep W and V in shared
     memory, large ones in global slots; empty matrices are not planned;
-    complex64 with flags bit 6 sends min(m, n) >= 128 to the multi-kernel
-    batch."""
+    with flags bit 6 complex64 sends min(m, n) >= 112 to the multi-kernel
+    batch, and with bits 6 and 10 real FP32 sends min(m, n) >= 144."""
     import numpy as np
     import paper_2601_17979_gb300 as bsvd
     shapes = [(8, 8), (30, 20), (100, 64), (512, 400), (0, 5), (12, 300), (47, 47)]
@@ -229,6 +229,14 @@ def test_persistent_plan_host_logic():
     assert all(x == 8 for x, w in zip(nb2, where2) if w >= 0)
     _, where3, launches3 = bsvd.persistent_plan("s", shapes, flags=bsvd.FLAG_NO_ONCHIP)
     assert set(where3.tolist()) == {0, -1}
-    _, where4, _ = bsvd.persistent_plan("c", [(300, 150), (40, 30), (128, 128)], flags=bsvd.FLAG_SPLIT_LARGE)
-    assert where4.tolist()[0] == 2 and where4.tolist()[2] == 2 and where4.tolist()[1] == 1
+    _, where4, _ = bsvd.persistent_plan("c", [(300, 150), (40, 30), (128, 128), (112, 300), (200, 111)],
+                                        flags=bsvd.FLAG_SPLIT_LARGE)
+    assert where4.tolist()[0] == 2 and where4.tolist()[2] == 2 and where4.tolist()[3] == 2
+    assert where4.tolist()[1] == 1 and where4.tolist()[4] in (0, 1)
+    split32 = bsvd.FLAG_SPLIT_LARGE | bsvd.FLAG_SPLIT_F32
+    _, where5, _ = bsvd.persistent_plan("s", [(300, 144), (300, 143), (144, 144), (500, 160)], flags=split32)
+    assert where5.tolist()[0] == 2 and where5.tolist()[2] == 2 and where5.tolist()[3] == 2
+    assert where5.tolist()[1] in (0, 1)
+    _, where6, _ = bsvd.persistent_plan("s", [(300, 200)], flags=bsvd.FLAG_SPLIT_LARGE)   # FP32 needs bit 10
+    assert where6.tolist()[0] in (0, 1)
     assert np.all(nb >= 0)
