@@ -176,7 +176,8 @@ __global__ void __launch_bounds__(kBlkThreads) blk_gram_f32_tc(const BlockedArgs
             cp_async_wait<0>();
         }
         __syncthreads();
-        gram_block_acc<NB>(P[it & 1], KP, kc, 0, NB, bm, bn, sub, WPB, lane, acc);
+        if (bm <= bn)                           // blocks below the diagonal are mirrors
+            gram_block_acc<NB>(P[it & 1], KP, kc, 0, NB, bm, bn, sub, WPB, lane, acc);
         __syncthreads();                        // before this buffer is refilled
     }
 #pragma unroll
@@ -235,7 +236,8 @@ __global__ void __launch_bounds__(kBlkThreads) blk_gram_c64_tc(const BlockedArgs
             P[kk + c * KP] = kk < kc ? W[k0 + kk + (long long)col * M] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        gram_c64_block_acc<NB>(P, KP, kc, 0, NB, bm, bn, sub, WPB, lane, re, im);
+        if (bm <= bn)                           // blocks below the diagonal are mirrors
+            gram_c64_block_acc<NB>(P, KP, kc, 0, NB, bm, bn, sub, WPB, lane, re, im);
         __syncthreads();
     }
 #pragma unroll

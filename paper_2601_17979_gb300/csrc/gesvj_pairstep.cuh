@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(kPairThreads, pair_min_blocks<T>()) blk_pairst
             const T* Pc = P + (it & 1) * (L::kChunk / (int)sizeof(T));
 #pragma unroll
             for (int h = 0; h < H; ++h) {
+                if (bm > bn) break;            // blocks below the diagonal are mirrors
                 if constexpr (kCplx)
                     gram_c64_block_acc<NB>(Pc, KP, kc, 0, NB, bm, bn, (warp + h * NW) / NB2, WPB, lane, re[h], im[h]);
                 else

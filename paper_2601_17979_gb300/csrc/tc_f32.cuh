@@ -122,6 +122,7 @@ __device__ __forceinline__ void gram_f32_mma(const float* W, int ldw, int M, int
     const int warp = gt >> 5, lane = gt & 31, g = lane >> 2, t = lane & 3;
     if (warp >= NBLK * NBLK) return;
     const int bm = warp / NBLK, bn = warp % NBLK;
+    if (bm > bn) return;          // a block below the diagonal: the mirror of one above it
     float acc[2][4];
 #pragma unroll
     for (int j = 0; j < 2; ++j)
