@@ -60,11 +60,11 @@ KERNEL_SOURCES = {
 }
 TRAFFIC_PER_MATRIX = {
     # 128x64, gesvj_fused_kernel<double|float,16,2,128>: 2,000-matrix launches
-    ("fused", "tall128x64_f64", "1aaf66d2379b"): (137736960 + 143072256) / 2000,
-    ("fused", "tall128x64_f32", "1aaf66d2379b"): (65926400 + 40410624) / 2000,
+    ("fused", "tall128x64_f64", "8b18517283c6"): (137206528 + 143052800) / 2000,
+    ("fused", "tall128x64_f32", "8b18517283c6"): (65873920 + 40259328) / 2000,
     # the whole uneven step (every kernel of both types), 2,000-matrix case:
-    # 497.7 GB over the warm-up and the timed step
-    ("uneven", "uneven", "fa908dd456c8"): 497.71e9 / 2 / 2000,
+    # 497.6 GB over the warm-up and the timed step
+    ("uneven", "uneven", "490147fdfd01"): 497.60e9 / 2 / 2000,
 }
 
 
