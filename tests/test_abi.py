@@ -186,7 +186,7 @@ def test_flat_outputs_layout():
 
 def test_split_workspace_query(L):
     """Flags bit 6 on a persistent complex64 batch adds the variable-shape
-    multi-kernel workspace for the matrices with min(m, n) >= 128 only;
+    multi-kernel workspace for the matrices with min(m, n) >= 112 only;
     batches of the other types ignore the flag."""
     h = bsvd.handle()
     n = ctypes.c_size_t()
@@ -240,3 +240,14 @@ def test_persistent_plan_host_logic():
     _, where6, _ = bsvd.persistent_plan("s", [(300, 200)], flags=bsvd.FLAG_SPLIT_LARGE)   # FP32 needs bit 10
     assert where6.tolist()[0] in (0, 1)
     assert np.all(nb >= 0)
+
+
+def test_flag_range(L):
+    """bsvd_opts.flags takes bits 0-12 (bit 12: three kernels per round
+    instead of the pair step); a higher bit is an invalid option."""
+    assert binding.workspace_bytes("s", [(300, 200)], True, batch=2, flags=8191) > 0
+    # the pair step and the three kernels share one workspace layout
+    assert (binding.workspace_bytes("s", [(300, 200)], True, batch=2, flags=4096)
+            == binding.workspace_bytes("s", [(300, 200)], True, batch=2))
+    with pytest.raises(binding.BsvdError, match="INVALID"):
+        binding.workspace_bytes("s", [(300, 200)], True, batch=2, flags=8192)
