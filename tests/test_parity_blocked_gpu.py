@@ -201,10 +201,12 @@ def test_blocked_complex64_tensor_core_and_ffma(flags, m, n, nb):
 
 @pytest.mark.parametrize("dtype", [np.complex64, np.float32])
 @pytest.mark.parametrize("m,n,nb,extra", [(200, 150, 16, 0), (257, 33, 8, 0), (150, 260, 16, 0), (70, 200, 8, 0),
-                                          (333, 97, 16, bsvd.FLAG_WIDE_ANGLES), (96, 96, 8, bsvd.FLAG_NO_MASKS)])
+                                          (333, 97, 16, bsvd.FLAG_WIDE_ANGLES), (96, 96, 8, bsvd.FLAG_NO_MASKS),
+                                          (40, 24, 8, 0), (24, 60, 16, 0)])
 def test_pairstep_equals_three_kernels_bitwise(dtype, m, n, nb, extra):
     """The pair-step kernel performs each stage's operations in the order of
-    the three per-round kernels (flags bit 12): the same bits."""
+    the three per-round kernels (flags bit 12): the same bits; also with
+    fewer rows than one staged 64-row chunk."""
     rng = np.random.default_rng(m + 7 * n + nb + extra)
     if dtype == np.complex64:
         mats = [(rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))).astype(dtype) for _ in range(4)]
